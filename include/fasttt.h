@@ -1,0 +1,210 @@
+/*
+ * fasttt.h — C ABI of libfasttt.so, a GB300 (sm_103a) implementation of FastTT,
+ * the sparse tensor-train decomposition of Li, Yu and Batselier ("Faster Tensor
+ * Train Decomposition for Sparse Data").
+ *
+ * Conventions (Sec. 2 of the paper, 0-based here):
+ *   - a d-way tensor A has mode sizes n_1..n_d; its COO input is an int32 index
+ *     array of shape (d, nnz) in structure-of-arrays layout (mode k's indices are
+ *     the contiguous row k: idx[k*nnz + e]) and nnz values;
+ *   - TT core k (k = 1..d) is a row-major r_{k-1} x n_k x r_k array of doubles,
+ *     r_0 = r_d = 1; entry a(i) = G_1[i_1] G_2[i_2] ... G_d[i_d] (Sec. 2.3);
+ *   - the k-unfolding has rows (i_1..i_k) and columns (i_{k+1}..i_d), last index
+ *     fastest (Sec. 2.2).
+ *
+ * Pointers named d_* are device pointers (cudaMalloc / torch CUDA memory) on the
+ * current device; "host" pointers are ordinary host memory.  Every call runs its
+ * work on the caller's CUDA stream (NULL = the legacy default stream) and returns
+ * once its results are ready, unless stated otherwise.  No call falls back to
+ * the CPU: without a usable CUDA device every entry point returns FASTTT_ECUDA.
+ *
+ * Errors: every int-returning call returns FASTTT_OK (0) or a negative code
+ * below; fasttt_last_error() then gives a message (thread-local, valid until the
+ * thread's next call).  No C++ exception crosses this boundary.
+ */
+#ifndef FASTTT_H
+#define FASTTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FASTTT_MAX_D 64
+
+/* return codes */
+#define FASTTT_OK 0
+#define FASTTT_EINVAL (-1)   /* bad argument: index out of range, NaN/Inf value, d < 2, no nonzero ... */
+#define FASTTT_EDUP (-2)     /* the COO input repeats a coordinate */
+#define FASTTT_ENOMEM (-3)   /* a device allocation failed */
+#define FASTTT_ETIMEOUT (-4) /* an iteration hit its bound (Jacobi sweeps) */
+#define FASTTT_ENUMERIC (-5) /* non-finite intermediate in the dense rounding */
+#define FASTTT_ERANK (-6)    /* a dense intermediate would exceed the size limits */
+#define FASTTT_ECUDA (-7)    /* a CUDA runtime call failed (message has the CUDA error) */
+
+/* value / core dtypes */
+#define FASTTT_F64 0
+#define FASTTT_F32 1
+
+/* fasttt_opts.precision */
+#define FASTTT_PREC_FP64 0   /* every floating-point step in IEEE FP64 */
+
+/* fasttt_opts.rounding */
+#define FASTTT_STATIC 0      /* delta_k of eq. (11), Alg. 6 */
+#define FASTTT_DYNAMIC 1     /* the re-spent error budget of Alg. 8 */
+
+/* fasttt_opts.stage */
+#define FASTTT_STAGE_FULL 0  /* Alg. 7: exact TT, then TT-rounding */
+#define FASTTT_STAGE_EXACT 1 /* Alg. 4 only: the lossless exact sparse TT (no cores) */
+
+typedef struct fasttt_opts {
+  int p;              /* split point 1..d; 0 = choose by Alg. 9 (flop model, eq. (13)) */
+  int precision;      /* FASTTT_PREC_FP64 */
+  int rounding;       /* FASTTT_STATIC or FASTTT_DYNAMIC */
+  int depar_values;   /* 1: value Depar (Alg. 3, exact parallelism) of the middle unfolding; 0: off */
+  int stage;          /* FASTTT_STAGE_FULL or FASTTT_STAGE_EXACT */
+  int keep_intermediates; /* 1: keep group maps, middle COO, Depar factors, singular values */
+  int64_t max_rank;   /* > 0: cap every TT rank (fixed-rank variant, Sec. 3.4); 0: none */
+  int64_t max_sweeps; /* Jacobi sweep bound of the dense SVDs; 0 = default (40) */
+} fasttt_opts;
+
+/* Fills *opts with the defaults: p = 0, FP64, static rounding, value Depar on,
+ * full stage, no intermediates, no rank cap, default sweep bound. */
+void fasttt_default_opts(fasttt_opts* opts);
+
+typedef struct fasttt_stats {
+  int d, p;
+  int64_t nnz_in;            /* entries passed in */
+  int64_t nnz;               /* entries kept (explicit zeros dropped) */
+  int64_t dropped;           /* explicit zeros dropped */
+  int64_t R;                 /* nonzero p-fibers (eq. (4)) at the chosen p */
+  int64_t Rs[FASTTT_MAX_D];  /* R for every p = 1..d when Alg. 9 ran (index p-1), else 0 */
+  int64_t rt[FASTTT_MAX_D + 1];    /* r~_k after Alg. 4 (k = 0..d) */
+  int64_t ranks[FASTTT_MAX_D + 1]; /* r_k of the output (k = 0..d) */
+  int64_t beta_r, beta_c;    /* row / column classes of the middle unfolding (value Depar) */
+  int64_t jacobi_sweeps;     /* total Jacobi sweeps over all dense SVDs */
+  int64_t launches;          /* CUDA kernels this call launched */
+  double norm2;              /* ||A||_F^2 */
+  double err2;               /* sum over truncations of the discarded sigma^2 (||E_k||_F^2) */
+  double deltas[FASTTT_MAX_D + 1]; /* delta_k used at bond k (0 where unused) */
+  double ms_ingest, ms_group, ms_depar, ms_round, ms_total; /* CUDA-event stage times */
+  /* CUDA-event time and algorithmic work of the heavy kernel classes: FP64 GEMM
+   * (2MNK flops), Jacobi sweeps (dot products + applied rotations, flops) and
+   * radix-sort passes (key/value bytes moved) */
+  double ms_gemm, flop_gemm, ms_jacobi, flop_jacobi, ms_sort, bytes_sort;
+} fasttt_stats;
+
+typedef struct fasttt_tt fasttt_tt; /* opaque result handle */
+
+/*
+ * fasttt_decompose — Alg. 7 (FastTT): Alg. 4 with Alg. 5 (exact grouping of the
+ * sparse unfoldings into quasi-permutation cores, Sec. 3.1-3.2), value Depar of
+ * the middle unfolding (Alg. 3 with exact parallelism), then Alg. 6 (or Alg. 8)
+ * TT-rounding to relative accuracy eps (Sec. 3.3-3.5).
+ *
+ *  d, dims      order d (2..FASTTT_MAX_D) and host array of the d mode sizes (>= 1);
+ *  nnz, d_idx   number of COO entries and their (d, nnz) int32 indices, 0-based;
+ *  d_vals       nnz values, FASTTT_F64 or FASTTT_F32 (upcast exactly to FP64);
+ *  eps          relative accuracy (>= 0); eps = 0 keeps the numerical ranks
+ *               (sigma_i > max(M,N) 2^-52 sigma_1, M x N the unfolding's size);
+ *  opts         NULL for the defaults;
+ *  stream       cudaStream_t (NULL = default stream);
+ *  out          receives a handle owned by the caller (free with fasttt_tt_free);
+ *  stats        optional (may be NULL), filled on success and, as far as known,
+ *               on failure.
+ * Inputs are borrowed and only read; they must stay valid until the call returns.
+ * Errors: EINVAL (bad sizes, index out of range, NaN/Inf, all-zero tensor),
+ * EDUP (repeated coordinate), ENOMEM, ERANK, ETIMEOUT, ENUMERIC, ECUDA.
+ */
+int fasttt_decompose(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx,
+                     const void* d_vals, int val_dtype, double eps, const fasttt_opts* opts,
+                     void* stream, fasttt_tt** out, fasttt_stats* stats);
+
+/* Releases a handle and all device memory it owns (NULL is a no-op). */
+void fasttt_tt_free(fasttt_tt* tt);
+
+/* Copies the handle's statistics into *stats. */
+int fasttt_tt_stats(const fasttt_tt* tt, fasttt_stats* stats);
+
+/* Copies the d+1 TT ranks r_0..r_d into the host array ranks. */
+int fasttt_tt_ranks(const fasttt_tt* tt, int64_t* ranks);
+
+/* Borrowed device pointer to core k (1..d), r_{k-1} x n_k x r_k FP64 row-major;
+ * valid until fasttt_tt_free. */
+int fasttt_tt_core(const fasttt_tt* tt, int k, const double** d_core);
+
+/* Arrays a handle can hand out with fasttt_tt_count / fasttt_tt_copy.  k is the
+ * core index (1..d) or the bond index where noted; ignored otherwise. */
+#define FASTTT_ARR_CORE 0        /* f64, core k (r_{k-1} n_k r_k) */
+#define FASTTT_ARR_LEFT_PARENT 1 /* i32, core k < p: alpha_{k-1} of every alpha_k (r~_k) */
+#define FASTTT_ARR_LEFT_INDEX 2  /* i32, core k < p: i_k of every alpha_k (r~_k) */
+#define FASTTT_ARR_RIGHT_INDEX 3 /* i32, core k > p: i_k of every alpha_{k-1} (r~_{k-1}) */
+#define FASTTT_ARR_RIGHT_CHILD 4 /* i32, core k > p: alpha_k of every alpha_{k-1} (r~_{k-1}) */
+#define FASTTT_ARR_MID_ROW 5     /* i64, middle unfolding X entries sorted by (row, col) */
+#define FASTTT_ARR_MID_COL 6     /* i64 */
+#define FASTTT_ARR_MID_VAL 7     /* f64 */
+#define FASTTT_ARR_ROW_ID 8      /* i64, nonzero rows of X ascending */
+#define FASTTT_ARR_ROW_CLASS 9   /* i32, value-Depar class of each nonzero row */
+#define FASTTT_ARR_ROW_PREF 10   /* f64, prefactor (first nonzero) of each nonzero row */
+#define FASTTT_ARR_COL_ID 11     /* i64, nonzero columns of X ascending */
+#define FASTTT_ARR_COL_CLASS 12  /* i32 */
+#define FASTTT_ARR_COL_PREF 13   /* f64 */
+#define FASTTT_ARR_DP_ROW 14     /* i32, entries of D' (beta_r x beta_c) sorted by (row, col) */
+#define FASTTT_ARR_DP_COL 15     /* i32 */
+#define FASTTT_ARR_DP_VAL 16     /* f64 */
+#define FASTTT_ARR_LAM_S 17      /* f64, Lambda_S (beta_r) */
+#define FASTTT_ARR_LAM_T 18      /* f64, Lambda_T (beta_c) */
+#define FASTTT_ARR_SIGMA 19      /* f64, singular values computed at bond k, descending */
+
+/* Number of elements of array `what` (>= 0), or a negative error code
+ * (EINVAL when the array does not exist, e.g. intermediates were not kept). */
+int64_t fasttt_tt_count(const fasttt_tt* tt, int what, int k);
+
+/* Copies `count` elements of array `what` into dst (host or device memory;
+ * count must equal fasttt_tt_count). */
+int fasttt_tt_copy(const fasttt_tt* tt, int what, int k, void* dst, int64_t count);
+
+/*
+ * tt_eval_at — entry evaluation (Sec. 2.3): out[e] = G_1[i_1^e] ... G_d[i_d^e]
+ * for m index tuples.
+ *  d, dims, ranks   host arrays: d mode sizes, d+1 ranks (r_0 = r_d = 1);
+ *  d_cores          host array of d device pointers, core k row-major r_{k-1} x n_k x r_k;
+ *  dtype            FASTTT_F64 or FASTTT_F32 (cores and output alike);
+ *  m, d_idx         (d, m) int32 indices, structure-of-arrays, 0-based;
+ *  d_out            m outputs.
+ * Ranks up to 8192 are supported (ERANK beyond).  Indices are range-checked on the
+ * device; a bad index makes the call return EINVAL (outputs then unspecified).
+ */
+int tt_eval_at(int d, const int64_t* dims, const int64_t* ranks, const void* const* d_cores,
+               int dtype, int64_t m, const int32_t* d_idx, void* d_out, void* stream);
+
+/*
+ * tt_eval_backward — adjoint of tt_eval_at: for L = sum_e g_e a(i^e),
+ *   dL/dG_k[i] = sum_{e: i_k^e = i} g_e L_{k-1}(e)^T R_{k+1}(e),
+ * L/R the left/right partial products of the chain.  d_grad_cores is a host
+ * array of d device pointers shaped like the cores; gradients are ADDED to them
+ * (zero them first for a plain gradient).  recompute = 1 recomputes the right
+ * partial products per mode instead of storing all of them
+ * (O(m * max r) scratch instead of O(m * sum r)).
+ */
+int tt_eval_backward(int d, const int64_t* dims, const int64_t* ranks,
+                     const void* const* d_cores, int dtype, int64_t m, const int32_t* d_idx,
+                     const void* d_grad_out, void* const* d_grad_cores, int recompute,
+                     void* stream);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* fasttt_last_error(void);
+
+/* Library version string. */
+const char* fasttt_version(void);
+
+/* Test hook for the host-side failure paths: the n-th device allocation from now
+ * (n >= 1) fails with ENOMEM; n = 0 disables it.  Affects the calling process. */
+void fasttt_debug_fail_alloc_after(int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTTT_H */

@@ -1,0 +1,695 @@
+// libfasttt C ABI and the host orchestration of Alg. 7 (FastTT):
+// S1 ingest -> S2-S5 grouping (Alg. 9, Alg. 4/5) -> S6 value Depar (Alg. 3)
+// -> S7-S11 TT-rounding (Alg. 6 / Alg. 8) -> S12 output cores.
+//
+// The quasi-permutation cores of Alg. 4 are never materialised as 0/1 arrays:
+// multiplying a factor into one is a gather (first SVD sweep, G_{k+1} x_1 W) or
+// a scatter (second SVD sweep, G_{k-1} x_3 (V Sigma)) on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dense.cuh"
+#include "depar.cuh"
+#include "group.cuh"
+
+namespace fasttt {
+
+// ---------------------------------------------------------------- allocation with the test hook
+
+namespace {
+std::mutex g_alloc_mu;
+int64_t g_fail_after = 0;  // 0 = off
+thread_local std::string g_last_error;
+// Set while a handle is released: its buffers may belong to a stream the caller
+// has destroyed since, so they are freed synchronously instead.
+thread_local bool g_free_sync = false;
+}  // namespace
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_fail_after > 0 && --g_fail_after == 0) fail(FASTTT_ENOMEM, "injected allocation failure");
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    fail(e == cudaErrorMemoryAllocation ? FASTTT_ENOMEM : FASTTT_ECUDA, buf);
+  }
+  return p;
+}
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+thread_local std::vector<KClock> g_clocks;
+}  // namespace
+
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+void kclock_begin(KClock& c, int cls, cudaStream_t s) {
+  c.cls = cls;
+  cudaEventCreate(&c.a);
+  cudaEventCreate(&c.b);
+  cudaEventRecord(c.a, s);
+}
+
+void kclock_end(KClock& c, double work, cudaStream_t s) {
+  c.work = work;
+  cudaEventRecord(c.b, s);
+  g_clocks.push_back(c);
+  c.a = c.b = nullptr;
+}
+
+void kclock_reset() {
+  for (auto& c : g_clocks) {
+    if (c.a) cudaEventDestroy(c.a);
+    if (c.b) cudaEventDestroy(c.b);
+  }
+  g_clocks.clear();
+}
+
+void kclock_collect(double ms[KC_COUNT], double work[KC_COUNT]) {
+  for (int i = 0; i < KC_COUNT; ++i) ms[i] = work[i] = 0.0;
+  for (auto& c : g_clocks) {
+    float t = 0.f;
+    if (cudaEventSynchronize(c.b) == cudaSuccess && cudaEventElapsedTime(&t, c.a, c.b) == cudaSuccess) {
+      ms[c.cls] += t;
+      work[c.cls] += c.work;
+    }
+  }
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (!p) return;
+  if (g_free_sync) cudaFree(p);
+  else cudaFreeAsync(p, s);
+}
+
+namespace {
+
+#define GRID_STRIDE(i, n)                                                            \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------- factor kernels
+
+// C (beta_r x beta_c row-major) = Lambda_S D' Lambda_T, entry (lam_s * d') * lam_t
+__global__ void build_C_kernel(const int32_t* dp_row, const int32_t* dp_col, const double* dp_val, int64_t n,
+                               const double* lam_s, const double* lam_t, int64_t ldc, double* C) {
+  GRID_STRIDE(e, n) {
+    const int32_t g = dp_row[e], h = dp_col[e];
+    C[(int64_t)g * ldc + h] = (lam_s[g] * dp_val[e]) * lam_t[h];
+  }
+}
+
+// out (ld-wide rows): row ids[t] = (pref[t] / lam[cls[t]]) * src[cls[t], :r]   (Q_S U_C)
+__global__ void expand_rows_kernel(const int64_t* ids, const int32_t* cls, const double* pref,
+                                   const double* lam, int64_t nz, const double* src, int64_t r,
+                                   double* out) {
+  GRID_STRIDE(e, nz * r) {
+    const int64_t t = e / r, a = e % r;
+    const int32_t g = cls[t];
+    out[ids[t] * r + a] = (pref[t] / lam[g]) * src[(int64_t)g * r + a];
+  }
+}
+
+// out (r x ncols row-major): column ids[u] = sigma * Vt[:, cls[u]] * (pref[u]/lam[cls[u]])   (Sigma V^T Q_T)
+__global__ void expand_cols_kernel(const int64_t* ids, const int32_t* cls, const double* pref,
+                                   const double* lam, int64_t nz, const double* Vt, int64_t ldv,
+                                   const double* sigma, int64_t r, int64_t ncols, double* out) {
+  GRID_STRIDE(e, nz * r) {
+    const int64_t u = e / r, a = e % r;
+    const int32_t h = cls[u];
+    out[a * ncols + ids[u]] = sigma[a] * Vt[a * ldv + h] * (pref[u] / lam[h]);
+  }
+}
+
+// G_k (r x n x rnext) from a right quasi-permutation core: column (ridx[al], rchild[al]) of
+// unfold_1(G_k) = W[:, al]  (the first-sweep merge G_k x_1 W)
+__global__ void merge_right_kernel(const double* W, int64_t r, int64_t rt_prev, const int32_t* ridx,
+                                   const int32_t* rchild, int64_t n, int64_t rnext, double* G) {
+  GRID_STRIDE(e, r * rt_prev) {
+    const int64_t a = e / rt_prev, al = e % rt_prev;
+    G[(a * n + ridx[al]) * rnext + rchild[al]] = W[a * rt_prev + al];
+  }
+}
+
+// G_k (rprev x n x r) from a left quasi-permutation core: row (lpar[al], lidx[al]) of
+// unfold_2(G_k) = VS[al, :]  (the second-sweep merge G_k x_3 (V Sigma))
+__global__ void merge_left_kernel(const double* VS, int64_t rt_k, int64_t r, const int32_t* lpar,
+                                  const int32_t* lidx, int64_t n, double* G) {
+  GRID_STRIDE(e, rt_k * r) {
+    const int64_t al = e / r, a = e % r;
+    G[((int64_t)lpar[al] * n + lidx[al]) * r + a] = VS[al * r + a];
+  }
+}
+
+// out (M x r) = U (M x r) scaled column-wise by sigma
+__global__ void scale_cols_kernel(const double* U, int64_t M, int64_t r, const double* sigma, double* out) {
+  GRID_STRIDE(e, M * r) out[e] = U[e] * sigma[e % r];
+}
+
+// out (r x N) = sigma (row-wise) * Vt
+__global__ void scale_rows_kernel(const double* Vt, int64_t r, int64_t N, const double* sigma, double* out) {
+  GRID_STRIDE(e, r * N) out[e] = Vt[e] * sigma[e / N];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- handle
+
+struct Handle {
+  int d = 0;
+  std::vector<int64_t> dims, ranks;
+  std::vector<DBuf<double>> cores;
+  fasttt_stats st{};
+  bool kept = false;
+  Grouped grp;
+  DeparResult dep;
+  std::vector<std::vector<double>> sigmas;  // per bond (index k), host copies
+};
+
+}  // namespace fasttt
+
+struct fasttt_tt {
+  fasttt::Handle h;
+};
+
+namespace fasttt {
+int tt_eval_at_impl(int d, const int64_t* dims, const int64_t* ranks, const void* const* cores, int dtype, int64_t m,
+                    const int32_t* idx, void* out, cudaStream_t s);
+int tt_eval_backward_impl(int d, const int64_t* dims, const int64_t* ranks, const void* const* cores, int dtype,
+                          int64_t m, const int32_t* idx, const void* gout, void* const* grads, int recompute,
+                          cudaStream_t s);
+}  // namespace fasttt
+
+namespace fasttt {
+namespace {
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  double lap() {  // ms since construction / last lap
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    std::swap(a, b);
+    return ms;
+  }
+};
+
+// rank rule S11: smallest r >= 1 with sqrt(sum_{i>r} s_i^2) <= delta (tails summed
+// from the smallest value up); eps = 0: s_i > max(M,N) 2^-52 s_1 for the full
+// k-unfolding of A; capped by max_rank.
+int64_t rank_rule(const std::vector<double>& s, double delta, bool eps_zero, const std::vector<int64_t>& dims,
+                  int bond, int64_t max_rank) {
+  const int64_t n = (int64_t)s.size();
+  int64_t r = n;
+  if (!eps_zero) {
+    std::vector<double> tail(n + 1, 0.0);
+    double acc = 0.0;
+    for (int64_t i = n - 1; i >= 0; --i) {
+      acc += s[i] * s[i];
+      tail[i] = acc;
+    }
+    const double d2 = delta * delta;
+    for (int64_t c = 1; c <= n; ++c)
+      if (tail[c] <= d2) { r = c; break; }
+  } else {
+    // max(prod(n_1..n_k), prod(n_{k+1}..n_d)) as a double (exact integers up to 2^53)
+    double a = 1.0, b = 1.0;
+    for (int k = 0; k < bond; ++k) a *= (double)dims[k];
+    for (int k = bond; k < (int)dims.size(); ++k) b *= (double)dims[k];
+    const double tol = std::max(a, b) * 0x1p-52 * (n ? s[0] : 0.0);
+    int64_t c = 0;
+    for (double x : s) c += (x > tol) ? 1 : 0;
+    r = std::max<int64_t>(1, c);
+  }
+  if (max_rank > 0) r = std::min(r, max_rank);
+  return r;
+}
+
+void finish_stats(fasttt_stats& st, int64_t launches0) {
+  double ms[KC_COUNT], work[KC_COUNT];
+  kclock_collect(ms, work);
+  st.ms_gemm = ms[KC_GEMM];
+  st.flop_gemm = work[KC_GEMM];
+  st.ms_jacobi = ms[KC_JACOBI];
+  st.flop_jacobi = work[KC_JACOBI];
+  st.ms_sort = ms[KC_SORT];
+  st.bytes_sort = work[KC_SORT];
+  kclock_reset();
+  st.launches = launch_count() - launches0;
+}
+
+double tail2(const std::vector<double>& s, int64_t r) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)s.size() - 1; i >= r; --i) acc += s[i] * s[i];
+  return acc;
+}
+
+void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const void* d_vals, int val_dtype,
+         double eps, const fasttt_opts& o, cudaStream_t s, Handle& H) {
+  if (!(eps >= 0.0) || !std::isfinite(eps)) fail(FASTTT_EINVAL, "eps must be finite and >= 0");
+  if (o.rounding != FASTTT_STATIC && o.rounding != FASTTT_DYNAMIC) fail(FASTTT_EINVAL, "bad rounding mode");
+  if (o.precision != FASTTT_PREC_FP64) fail(FASTTT_EINVAL, "unsupported precision");
+  if (o.stage != FASTTT_STAGE_FULL && o.stage != FASTTT_STAGE_EXACT) fail(FASTTT_EINVAL, "bad stage");
+  const int64_t max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
+  fasttt_stats& st = H.st;
+  st.d = d;
+  kclock_reset();
+  const int64_t launches0 = launch_count();
+  Timer total(s), lap(s);
+  // S1
+  Ingested in;
+  ingest(d, dims, nnz, d_idx, d_vals, val_dtype, in, s);
+  st.nnz_in = in.nnz_in;
+  st.nnz = in.nnz;
+  st.dropped = in.dropped;
+  st.norm2 = in.norm2;
+  st.ms_ingest = lap.lap();
+  H.d = d;
+  H.dims = in.dims;
+  // S2-S5
+  Grouped& g = H.grp;
+  group(in, o.p, o.max_rank, g, s);
+  const int p = g.p;
+  st.p = p;
+  st.R = g.R;
+  for (size_t q = 0; q < g.Rs.size(); ++q) st.Rs[q] = g.Rs[q];
+  for (int k = 0; k <= d; ++k) st.rt[k] = g.rt[k];
+  st.ms_group = lap.lap();
+  in.idx.reset();
+  in.vals.reset();
+  if (o.stage == FASTTT_STAGE_EXACT) {
+    H.kept = true;
+    for (int k = 0; k <= d; ++k) st.ranks[k] = g.rt[k];
+    H.ranks.assign(g.rt.begin(), g.rt.end());
+    st.ms_total = total.lap();
+    finish_stats(st, launches0);
+    return;
+  }
+  // S6
+  DeparResult& dp = H.dep;
+  value_depar(g.mid_row.get(), g.mid_col.get(), g.mid_val.get(), in.nnz, g.mid_cols, o.depar_values != 0, dp, s);
+  st.beta_r = dp.rows.beta;
+  st.beta_c = dp.cols.beta;
+  st.ms_depar = lap.lap();
+
+  // S7-S11
+  const std::vector<int64_t>& n = H.dims;
+  const double normA = std::sqrt(in.norm2);
+  const bool eps0 = (eps == 0.0);
+  const double c = std::sqrt((double)(p - 1)) + std::sqrt((double)(d - p));
+  double d_right = std::sqrt((double)(d - p)) / c * eps * normA;   // Alg. 8 budgets
+  double d_left = std::sqrt((double)(p - 1)) / c * eps * normA;
+  auto delta_for = [&](int bond, bool right_side) {
+    if (o.rounding == FASTTT_STATIC) return eps * normA / c;                      // eq. (11)
+    return right_side ? d_right / std::sqrt((double)(d - bond)) : d_left / std::sqrt((double)bond);
+  };
+  H.sigmas.assign(d + 1, {});
+  std::vector<int64_t> r(d + 1, 1);
+  for (int k = 0; k <= d; ++k) r[k] = g.rt[k];
+  std::vector<DBuf<double>> G(d + 1);  // 1-based dense cores
+  double err2 = 0.0;
+  auto record = [&](int bond, const SvdOut& sv, double dl) {
+    const double e2 = tail2(sv.sigma_all, sv.r);
+    err2 += e2;
+    st.deltas[bond] = dl;
+    st.jacobi_sweeps += sv.sweeps;
+    if (o.keep_intermediates) H.sigmas[bond] = sv.sigma_all;
+    return e2;
+  };
+  // --- the first SVD, on C = Lambda_S D' Lambda_T
+  {
+    const int64_t br = dp.rows.beta, bc = dp.cols.beta;
+    if ((double)br * (double)bc > 4.0e9) fail(FASTTT_ERANK, "value-Depar factor C too large for the dense SVD");
+    DBuf<double> C((size_t)br * bc, s);
+    FTT_CUDA(cudaMemsetAsync(C.get(), 0, C.bytes(), s));
+    build_C_kernel<<<grid_for(dp.dp_n), 256, 0, s>>>(dp.dp_row.get(), dp.dp_col.get(), dp.dp_val.get(), dp.dp_n,
+                                                     dp.rows.lam.get(), dp.cols.lam.get(), bc, C.get());
+    FTT_LAUNCH();
+    const int bond = (p < d) ? p : d - 1;
+    const double dl = delta_for(bond, p < d);
+    SvdOut sv;
+    svd_truncated(C.get(), br, bc, [&](const std::vector<double>& sg) {
+      return rank_rule(sg, dl, eps0, n, bond, o.max_rank);
+    }, max_sweeps, sv, s);
+    C.reset();
+    const double e2 = record(bond, sv, dl);
+    const int64_t rr = sv.r;
+    // U_X = Q_S U_C (mid_rows x rr), V-side: Sigma V_C^T Q_T (rr x mid_cols)
+    DBuf<double> UX((size_t)g.mid_rows * rr, s);
+    FTT_CUDA(cudaMemsetAsync(UX.get(), 0, UX.bytes(), s));
+    expand_rows_kernel<<<grid_for(dp.rows.nz * rr), 256, 0, s>>>(
+        dp.rows.ids.get(), dp.rows.cls.get(), dp.rows.pref.get(), dp.rows.lam.get(), dp.rows.nz, sv.U.get(), rr,
+        UX.get());
+    FTT_LAUNCH();
+    DBuf<double> SW((size_t)rr * g.mid_cols, s);
+    FTT_CUDA(cudaMemsetAsync(SW.get(), 0, SW.bytes(), s));
+    expand_cols_kernel<<<grid_for(dp.cols.nz * rr), 256, 0, s>>>(
+        dp.cols.ids.get(), dp.cols.cls.get(), dp.cols.pref.get(), dp.cols.lam.get(), dp.cols.nz, sv.Vt.get(), bc,
+        sv.sigma.get(), rr, g.mid_cols, SW.get());
+    FTT_LAUNCH();
+    if (p < d) {
+      // G_p := U_X ; G_{p+1} := G_{p+1} x_1 (Sigma V^T)  (right quasi-permutation core)
+      G[p] = std::move(UX);
+      r[p] = rr;
+      const int k1 = p + 1;
+      DBuf<double> Gn((size_t)rr * n[k1 - 1] * r[k1], s);
+      FTT_CUDA(cudaMemsetAsync(Gn.get(), 0, Gn.bytes(), s));
+      merge_right_kernel<<<grid_for(rr * g.rt[p]), 256, 0, s>>>(SW.get(), rr, g.rt[p], g.right_index[0].get(),
+                                                                 g.right_child[0].get(), n[k1 - 1], r[k1], Gn.get());
+      FTT_LAUNCH();
+      G[k1] = std::move(Gn);
+      if (o.rounding == FASTTT_DYNAMIC) d_right = std::sqrt(std::max(d_right * d_right - e2, 0.0));
+    } else {
+      // p = d: G_d := U_X^T (r x n_d x 1); G_{d-1} := G_{d-1} x_3 (V Sigma) (left quasi-permutation core)
+      DBuf<double> Gd((size_t)rr * n[d - 1], s);
+      transpose_f64(UX.get(), g.mid_rows, rr, Gd.get(), s);
+      G[d] = std::move(Gd);
+      r[d - 1] = rr;
+      DBuf<double> VS((size_t)g.mid_cols * rr, s);
+      transpose_f64(SW.get(), rr, g.mid_cols, VS.get(), s);
+      const int k0 = d - 1;
+      DBuf<double> Gp((size_t)r[k0 - 1] * n[k0 - 1] * rr, s);
+      FTT_CUDA(cudaMemsetAsync(Gp.get(), 0, Gp.bytes(), s));
+      merge_left_kernel<<<grid_for(g.rt[k0] * rr), 256, 0, s>>>(VS.get(), g.rt[k0], rr, g.left_parent[k0 - 1].get(),
+                                                                 g.left_index[k0 - 1].get(), n[k0 - 1], Gp.get());
+      FTT_LAUNCH();
+      G[k0] = std::move(Gp);
+      if (o.rounding == FASTTT_DYNAMIC) d_left = std::sqrt(std::max(d_left * d_left - e2, 0.0));
+    }
+  }
+  int start;
+  if (p < d) {
+    // --- first SVD sweep k = p+1..d-1 (Alg. 6)
+    for (int k = p + 1; k <= d - 1; ++k) {
+      const int64_t M = r[k - 1] * n[k - 1], N = r[k];
+      const double dl = delta_for(k, true);
+      SvdOut sv;
+      svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) {
+        return rank_rule(sg, dl, eps0, n, k, o.max_rank);
+      }, max_sweeps, sv, s);
+      const double e2 = record(k, sv, dl);
+      const int64_t rr = sv.r;
+      G[k] = std::move(sv.U);
+      DBuf<double> W((size_t)rr * N, s);
+      scale_rows_kernel<<<grid_for(rr * N), 256, 0, s>>>(sv.Vt.get(), rr, N, sv.sigma.get(), W.get());
+      FTT_LAUNCH();
+      r[k] = rr;
+      const int k1 = k + 1;
+      DBuf<double> Gn((size_t)rr * n[k1 - 1] * r[k1], s);
+      FTT_CUDA(cudaMemsetAsync(Gn.get(), 0, Gn.bytes(), s));
+      merge_right_kernel<<<grid_for(rr * g.rt[k]), 256, 0, s>>>(W.get(), rr, g.rt[k], g.right_index[k - p].get(),
+                                                                 g.right_child[k - p].get(), n[k1 - 1], r[k1], Gn.get());
+      FTT_LAUNCH();
+      G[k1] = std::move(Gn);
+      if (o.rounding == FASTTT_DYNAMIC) d_right = std::sqrt(std::max(d_right * d_right - e2, 0.0));
+    }
+    // --- QR sweep k = d..p+1: unfold_1^T(G_k) = Q R by an untruncated SVD of
+    // unfold_1(G_k) = U S V^T (Q = V, R = S U^T); G_{k-1} := G_{k-1} x_3 R^T
+    for (int k = d; k >= p + 1; --k) {
+      const int64_t M = r[k - 1], N = n[k - 1] * r[k];
+      SvdOut sv;
+      svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) { return (int64_t)sg.size(); },
+                    max_sweeps, sv, s);
+      st.jacobi_sweeps += sv.sweeps;
+      const int64_t q = sv.r;
+      G[k] = std::move(sv.Vt);
+      DBuf<double> US((size_t)M * q, s);
+      scale_cols_kernel<<<grid_for(M * q), 256, 0, s>>>(sv.U.get(), M, q, sv.sigma.get(), US.get());
+      FTT_LAUNCH();
+      const int64_t Mp = r[k - 2] * n[k - 2];
+      DBuf<double> Gp((size_t)Mp * q, s);
+      gemm_f64(Mp, q, M, 1.0, G[k - 1].get(), M, 1, US.get(), q, 1, 0.0, Gp.get(), q, 1, s);
+      G[k - 1] = std::move(Gp);
+      r[k - 1] = q;
+    }
+    start = p;
+  } else {
+    start = d - 1;
+  }
+  // --- second SVD sweep k = start..2: SVD of unfold_1^T(G_k) via unfold_1(G_k) = U S V^T:
+  // G_k := V^T rows, G_{k-1} := G_{k-1} x_3 (U S)  (left quasi-permutation core)
+  for (int k = start; k >= 2; --k) {
+    const int64_t M = r[k - 1], N = n[k - 1] * r[k];
+    const double dl = delta_for(k - 1, false);
+    SvdOut sv;
+    svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) {
+      return rank_rule(sg, dl, eps0, n, k - 1, o.max_rank);
+    }, max_sweeps, sv, s);
+    const double e2 = record(k - 1, sv, dl);
+    const int64_t rr = sv.r;
+    G[k] = std::move(sv.Vt);
+    DBuf<double> US((size_t)M * rr, s);
+    scale_cols_kernel<<<grid_for(M * rr), 256, 0, s>>>(sv.U.get(), M, rr, sv.sigma.get(), US.get());
+    FTT_LAUNCH();
+    const int k0 = k - 1;
+    DBuf<double> Gp((size_t)r[k0 - 1] * n[k0 - 1] * rr, s);
+    FTT_CUDA(cudaMemsetAsync(Gp.get(), 0, Gp.bytes(), s));
+    merge_left_kernel<<<grid_for(g.rt[k0] * rr), 256, 0, s>>>(US.get(), g.rt[k0], rr, g.left_parent[k0 - 1].get(),
+                                                               g.left_index[k0 - 1].get(), n[k0 - 1], Gp.get());
+    FTT_LAUNCH();
+    G[k0] = std::move(Gp);
+    r[k0] = rr;
+    if (o.rounding == FASTTT_DYNAMIC) d_left = std::sqrt(std::max(d_left * d_left - e2, 0.0));
+  }
+  // S12
+  st.err2 = err2;
+  H.cores.clear();
+  for (int k = 1; k <= d; ++k) H.cores.push_back(std::move(G[k]));
+  H.ranks.assign(d + 1, 1);
+  for (int k = 1; k < d; ++k) H.ranks[k] = r[k];
+  for (int k = 0; k <= d; ++k) st.ranks[k] = H.ranks[k];
+  H.kept = o.keep_intermediates != 0;
+  if (!H.kept) {
+    H.grp = Grouped();
+    H.dep = DeparResult();
+  }
+  st.ms_round = lap.lap();
+  st.ms_total = total.lap();
+  finish_stats(st, launches0);
+}
+
+int handle_error(const Error& e) {
+  g_last_error = e.what();
+  return e.code;
+}
+
+}  // namespace
+}  // namespace fasttt
+
+using namespace fasttt;
+
+extern "C" {
+
+void fasttt_default_opts(fasttt_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->p = 0;
+  o->precision = FASTTT_PREC_FP64;
+  o->rounding = FASTTT_STATIC;
+  o->depar_values = 1;
+  o->stage = FASTTT_STAGE_FULL;
+  o->keep_intermediates = 0;
+  o->max_rank = 0;
+  o->max_sweeps = 0;
+}
+
+int fasttt_decompose(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const void* d_vals,
+                     int val_dtype, double eps, const fasttt_opts* opts, void* stream, fasttt_tt** out,
+                     fasttt_stats* stats) {
+  g_last_error.clear();
+  if (!out || !dims) {
+    g_last_error = "null argument";
+    return FASTTT_EINVAL;
+  }
+  *out = nullptr;
+  fasttt_opts o;
+  if (opts) o = *opts;
+  else fasttt_default_opts(&o);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::unique_ptr<fasttt_tt> tt(new fasttt_tt());
+  int rc = FASTTT_OK;
+  try {
+    run(d, dims, nnz, d_idx, d_vals, val_dtype, eps, o, s, tt->h);
+  } catch (const Error& e) {
+    rc = handle_error(e);
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    rc = FASTTT_ECUDA;
+  }
+  if (stats) *stats = tt->h.st;
+  if (rc != FASTTT_OK) {
+    cudaStreamSynchronize(s);
+    return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("CUDA error: ") + cudaGetErrorString(e);
+    return FASTTT_ECUDA;
+  }
+  *out = tt.release();
+  return FASTTT_OK;
+}
+
+void fasttt_tt_free(fasttt_tt* tt) {
+  if (!tt) return;
+  cudaDeviceSynchronize();
+  g_free_sync = true;
+  delete tt;
+  g_free_sync = false;
+}
+
+int fasttt_tt_stats(const fasttt_tt* tt, fasttt_stats* st) {
+  if (!tt || !st) return FASTTT_EINVAL;
+  *st = tt->h.st;
+  return FASTTT_OK;
+}
+
+int fasttt_tt_ranks(const fasttt_tt* tt, int64_t* ranks) {
+  if (!tt || !ranks) return FASTTT_EINVAL;
+  for (int k = 0; k <= tt->h.d; ++k) ranks[k] = tt->h.ranks[k];
+  return FASTTT_OK;
+}
+
+int fasttt_tt_core(const fasttt_tt* tt, int k, const double** d_core) {
+  if (!tt || !d_core || k < 1 || k > tt->h.d || tt->h.cores.empty()) return FASTTT_EINVAL;
+  *d_core = tt->h.cores[k - 1].get();
+  return FASTTT_OK;
+}
+
+namespace {
+struct ArrRef {
+  const void* p = nullptr;
+  int64_t n = -1;
+  size_t elem = 0;
+};
+
+ArrRef lookup(const fasttt_tt* tt, int what, int k) {
+  ArrRef a;
+  if (!tt) return a;
+  const Handle& H = tt->h;
+  const int p = H.st.p, d = H.d;
+  auto set = [&](const void* ptr, int64_t n, size_t e) { a.p = ptr; a.n = n; a.elem = e; };
+  switch (what) {
+    case FASTTT_ARR_CORE:
+      if (k >= 1 && k <= d && !H.cores.empty())
+        set(H.cores[k - 1].get(), H.ranks[k - 1] * H.dims[k - 1] * H.ranks[k], 8);
+      break;
+    case FASTTT_ARR_LEFT_PARENT:
+    case FASTTT_ARR_LEFT_INDEX:
+      if (H.kept && k >= 1 && k < p) {
+        const auto& b = (what == FASTTT_ARR_LEFT_PARENT) ? H.grp.left_parent[k - 1] : H.grp.left_index[k - 1];
+        set(b.get(), H.st.rt[k], 4);
+      }
+      break;
+    case FASTTT_ARR_RIGHT_INDEX:
+    case FASTTT_ARR_RIGHT_CHILD:
+      if (H.kept && k > p && k <= d) {
+        const auto& b = (what == FASTTT_ARR_RIGHT_INDEX) ? H.grp.right_index[k - p - 1] : H.grp.right_child[k - p - 1];
+        set(b.get(), H.st.rt[k - 1], 4);
+      }
+      break;
+    case FASTTT_ARR_MID_ROW: if (H.kept) set(H.grp.mid_row.get(), H.st.nnz, 8); break;
+    case FASTTT_ARR_MID_COL: if (H.kept) set(H.grp.mid_col.get(), H.st.nnz, 8); break;
+    case FASTTT_ARR_MID_VAL: if (H.kept) set(H.grp.mid_val.get(), H.st.nnz, 8); break;
+    case FASTTT_ARR_ROW_ID: if (H.kept && H.dep.rows.nz) set(H.dep.rows.ids.get(), H.dep.rows.nz, 8); break;
+    case FASTTT_ARR_ROW_CLASS: if (H.kept && H.dep.rows.nz) set(H.dep.rows.cls.get(), H.dep.rows.nz, 4); break;
+    case FASTTT_ARR_ROW_PREF: if (H.kept && H.dep.rows.nz) set(H.dep.rows.pref.get(), H.dep.rows.nz, 8); break;
+    case FASTTT_ARR_COL_ID: if (H.kept && H.dep.cols.nz) set(H.dep.cols.ids.get(), H.dep.cols.nz, 8); break;
+    case FASTTT_ARR_COL_CLASS: if (H.kept && H.dep.cols.nz) set(H.dep.cols.cls.get(), H.dep.cols.nz, 4); break;
+    case FASTTT_ARR_COL_PREF: if (H.kept && H.dep.cols.nz) set(H.dep.cols.pref.get(), H.dep.cols.nz, 8); break;
+    case FASTTT_ARR_DP_ROW: if (H.kept && H.dep.dp_n) set(H.dep.dp_row.get(), H.dep.dp_n, 4); break;
+    case FASTTT_ARR_DP_COL: if (H.kept && H.dep.dp_n) set(H.dep.dp_col.get(), H.dep.dp_n, 4); break;
+    case FASTTT_ARR_DP_VAL: if (H.kept && H.dep.dp_n) set(H.dep.dp_val.get(), H.dep.dp_n, 8); break;
+    case FASTTT_ARR_LAM_S: if (H.kept && H.dep.rows.beta) set(H.dep.rows.lam.get(), H.dep.rows.beta, 8); break;
+    case FASTTT_ARR_LAM_T: if (H.kept && H.dep.cols.beta) set(H.dep.cols.lam.get(), H.dep.cols.beta, 8); break;
+    case FASTTT_ARR_SIGMA:
+      if (H.kept && k >= 1 && k < d && k < (int)H.sigmas.size() && !H.sigmas[k].empty())
+        set(H.sigmas[k].data(), (int64_t)H.sigmas[k].size(), 8);
+      break;
+    default: break;
+  }
+  return a;
+}
+}  // namespace
+
+int64_t fasttt_tt_count(const fasttt_tt* tt, int what, int k) {
+  ArrRef a = lookup(tt, what, k);
+  if (a.n < 0) {
+    g_last_error = "array not available";
+    return FASTTT_EINVAL;
+  }
+  return a.n;
+}
+
+int fasttt_tt_copy(const fasttt_tt* tt, int what, int k, void* dst, int64_t count) {
+  ArrRef a = lookup(tt, what, k);
+  if (a.n < 0 || count != a.n || (!dst && count)) {
+    g_last_error = "array not available or count mismatch";
+    return FASTTT_EINVAL;
+  }
+  if (count == 0) return FASTTT_OK;
+  cudaError_t e = cudaMemcpy(dst, a.p, (size_t)count * a.elem, cudaMemcpyDefault);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("copy failed: ") + cudaGetErrorString(e);
+    return FASTTT_ECUDA;
+  }
+  return FASTTT_OK;
+}
+
+int tt_eval_at(int d, const int64_t* dims, const int64_t* ranks, const void* const* d_cores, int dtype, int64_t m,
+               const int32_t* d_idx, void* d_out, void* stream) {
+  g_last_error.clear();
+  try {
+    return tt_eval_at_impl(d, dims, ranks, d_cores, dtype, m, d_idx, d_out, static_cast<cudaStream_t>(stream));
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
+}
+
+int tt_eval_backward(int d, const int64_t* dims, const int64_t* ranks, const void* const* d_cores, int dtype,
+                     int64_t m, const int32_t* d_idx, const void* d_grad_out, void* const* d_grad_cores,
+                     int recompute, void* stream) {
+  g_last_error.clear();
+  try {
+    return tt_eval_backward_impl(d, dims, ranks, d_cores, dtype, m, d_idx, d_grad_out, d_grad_cores, recompute,
+                                 static_cast<cudaStream_t>(stream));
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
+}
+
+const char* fasttt_last_error(void) { return g_last_error.c_str(); }
+
+const char* fasttt_version(void) { return "fasttt-gb300 0.1 (sm_103a)"; }
+
+void fasttt_debug_fail_alloc_after(int64_t n) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_fail_after = n > 0 ? n : 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libfasttt.so (argument marshalling only).
+
+The names match the C ABI in include/fasttt.h: ``fasttt_decompose``,
+``tt_eval_at`` and ``tt_eval_backward``; every step of the computation runs in
+the library's CUDA kernels.  PyTorch only provides device memory and the CUDA
+stream.  Importing this module raises ImportError when the library has not been
+built (``python -m paper_1908_02721_gb300.build``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfasttt.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1908_02721_gb300.build`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+MAX_D = 64
+OK, EINVAL, EDUP, ENOMEM, ETIMEOUT, ENUMERIC, ERANK, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
+F64, F32 = 0, 1
+STATIC, DYNAMIC = 0, 1
+STAGE_FULL, STAGE_EXACT = 0, 1
+ARR = {name: i for i, name in enumerate([
+    "core", "left_parent", "left_index", "right_index", "right_child", "mid_row", "mid_col", "mid_val",
+    "row_id", "row_class", "row_pref", "col_id", "col_class", "col_pref", "dp_row", "dp_col", "dp_val",
+    "lam_s", "lam_t", "sigma"])}
+_ARR_DTYPE = {"core": torch.float64, "left_parent": torch.int32, "left_index": torch.int32,
+              "right_index": torch.int32, "right_child": torch.int32, "mid_row": torch.int64,
+              "mid_col": torch.int64, "mid_val": torch.float64, "row_id": torch.int64,
+              "row_class": torch.int32, "row_pref": torch.float64, "col_id": torch.int64,
+              "col_class": torch.int32, "col_pref": torch.float64, "dp_row": torch.int32,
+              "dp_col": torch.int32, "dp_val": torch.float64, "lam_s": torch.float64,
+              "lam_t": torch.float64, "sigma": torch.float64}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("rounding", ctypes.c_int),
+                ("depar_values", ctypes.c_int), ("stage", ctypes.c_int), ("keep_intermediates", ctypes.c_int),
+                ("max_rank", ctypes.c_int64), ("max_sweeps", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("p", ctypes.c_int), ("nnz_in", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("dropped", ctypes.c_int64), ("R", ctypes.c_int64), ("Rs", ctypes.c_int64 * MAX_D),
+                ("rt", ctypes.c_int64 * (MAX_D + 1)), ("ranks", ctypes.c_int64 * (MAX_D + 1)),
+                ("beta_r", ctypes.c_int64), ("beta_c", ctypes.c_int64), ("jacobi_sweeps", ctypes.c_int64),
+                ("launches", ctypes.c_int64),
+                ("norm2", ctypes.c_double), ("err2", ctypes.c_double),
+                ("deltas", ctypes.c_double * (MAX_D + 1)), ("ms_ingest", ctypes.c_double),
+                ("ms_group", ctypes.c_double), ("ms_depar", ctypes.c_double), ("ms_round", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("flop_gemm", ctypes.c_double),
+                ("ms_jacobi", ctypes.c_double), ("flop_jacobi", ctypes.c_double), ("ms_sort", ctypes.c_double),
+                ("bytes_sort", ctypes.c_double)]
+
+    def to_dict(self):
+        d = self.d
+        return {"d": d, "p": self.p, "nnz_in": self.nnz_in, "nnz": self.nnz, "dropped": self.dropped,
+                "R": self.R, "Rs": list(self.Rs[:d]), "rt": list(self.rt[:d + 1]),
+                "ranks": list(self.ranks[:d + 1]), "beta_r": self.beta_r, "beta_c": self.beta_c,
+                "jacobi_sweeps": self.jacobi_sweeps, "launches": self.launches, "norm2": self.norm2,
+                "err2": self.err2,
+                "deltas": list(self.deltas[:d + 1]), "ms_ingest": self.ms_ingest, "ms_group": self.ms_group,
+                "ms_depar": self.ms_depar, "ms_round": self.ms_round, "ms_total": self.ms_total,
+                "ms_gemm": self.ms_gemm, "flop_gemm": self.flop_gemm, "ms_jacobi": self.ms_jacobi,
+                "flop_jacobi": self.flop_jacobi, "ms_sort": self.ms_sort, "bytes_sort": self.bytes_sort}
+
+
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_lib.fasttt_default_opts.argtypes = [ctypes.POINTER(Opts)]
+_lib.fasttt_decompose.argtypes = [ctypes.c_int, _I64P, ctypes.c_int64, _P, _P, ctypes.c_int, ctypes.c_double,
+                                  ctypes.POINTER(Opts), _P, ctypes.POINTER(_P), ctypes.POINTER(Stats)]
+_lib.fasttt_decompose.restype = ctypes.c_int
+_lib.fasttt_tt_free.argtypes = [_P]
+_lib.fasttt_tt_stats.argtypes = [_P, ctypes.POINTER(Stats)]
+_lib.fasttt_tt_ranks.argtypes = [_P, _I64P]
+_lib.fasttt_tt_core.argtypes = [_P, ctypes.c_int, ctypes.POINTER(_P)]
+_lib.fasttt_tt_count.argtypes = [_P, ctypes.c_int, ctypes.c_int]
+_lib.fasttt_tt_count.restype = ctypes.c_int64
+_lib.fasttt_tt_copy.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int64]
+_lib.tt_eval_at.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64, _P, _P, _P]
+_lib.tt_eval_backward.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64,
+                                  _P, _P, ctypes.POINTER(_P), ctypes.c_int, _P]
+_lib.fasttt_last_error.restype = ctypes.c_char_p
+_lib.fasttt_version.restype = ctypes.c_char_p
+_lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
+
+EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_tt_stats", "fasttt_tt_ranks",
+           "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
+           "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after"]
+
+
+class FastTTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != OK:
+        raise FastTTError(rc, _lib.fasttt_last_error().decode())
+
+
+def version() -> str:
+    return _lib.fasttt_version().decode()
+
+
+def debug_fail_alloc_after(n: int) -> None:
+    _lib.fasttt_debug_fail_alloc_after(int(n))
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise FastTTError(ECUDA, "no CUDA device: libfasttt has no CPU path")
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x, dtype):
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x))
+    if x.device.type != "cuda" or x.dtype != dtype or not x.is_contiguous():
+        x = x.to(device="cuda", dtype=dtype).contiguous()
+    return x
+
+
+def _i64arr(vals):
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+class TT:
+    """Result handle of fasttt_decompose; owns the library's device memory."""
+
+    def __init__(self, handle, dims):
+        self._h = ctypes.c_void_p(handle)
+        self.dims = [int(n) for n in dims]
+        self.d = len(self.dims)
+        r = (ctypes.c_int64 * (self.d + 1))()
+        _check(_lib.fasttt_tt_ranks(self._h, r))
+        self.ranks = list(r)
+        st = Stats()
+        _check(_lib.fasttt_tt_stats(self._h, ctypes.byref(st)))
+        self.stats = st.to_dict()
+
+    def count(self, what, k=0) -> int:
+        n = _lib.fasttt_tt_count(self._h, ARR[what], int(k))
+        if n < 0:
+            raise FastTTError(int(n), _lib.fasttt_last_error().decode())
+        return int(n)
+
+    def array(self, what, k=0, device="cuda") -> torch.Tensor:
+        n = self.count(what, k)
+        out = torch.empty(n, dtype=_ARR_DTYPE[what], device=device)
+        if n:
+            _check(_lib.fasttt_tt_copy(self._h, ARR[what], int(k), ctypes.c_void_p(out.data_ptr()), n))
+        return out
+
+    def core(self, k, device="cuda") -> torch.Tensor:
+        """Copy of core k (1-based), shape (r_{k-1}, n_k, r_k)."""
+        return self.array("core", k, device).view(self.ranks[k - 1], self.dims[k - 1], self.ranks[k])
+
+    def cores(self, device="cuda"):
+        return [self.core(k, device) for k in range(1, self.d + 1)]
+
+    def free(self):
+        if self._h:
+            _lib.fasttt_tt_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True, rounding="static",
+                     stage="full", keep_intermediates=False, max_sweeps=0, stream=None) -> TT:
+    """FastTT (Alg. 7) of the COO tensor (idx (d, nnz) int32, vals float64/float32)."""
+    _require_cuda()
+    idx = _dev(idx, torch.int32)
+    if isinstance(vals, np.ndarray):
+        vals = torch.from_numpy(np.ascontiguousarray(vals))
+    vdtype = F32 if vals.dtype == torch.float32 else F64
+    vals = _dev(vals, torch.float32 if vdtype == F32 else torch.float64)
+    d = len(dims)
+    if idx.dim() != 2 or idx.shape[0] != d or vals.shape != (idx.shape[1],):
+        raise FastTTError(EINVAL, "idx must be (d, nnz) and vals (nnz,)")
+    o = Opts()
+    _lib.fasttt_default_opts(ctypes.byref(o))
+    o.p = int(p)
+    o.max_rank = int(max_rank)
+    o.depar_values = 1 if depar_values else 0
+    o.rounding = DYNAMIC if rounding == "dynamic" else STATIC
+    o.stage = STAGE_EXACT if stage == "exact" else STAGE_FULL
+    o.keep_intermediates = 1 if keep_intermediates else 0
+    o.max_sweeps = int(max_sweeps)
+    out = ctypes.c_void_p(0)
+    st = Stats()
+    rc = _lib.fasttt_decompose(d, _i64arr(dims), int(idx.shape[1]), ctypes.c_void_p(idx.data_ptr()),
+                               ctypes.c_void_p(vals.data_ptr()), vdtype, float(eps), ctypes.byref(o),
+                               _stream(stream), ctypes.byref(out), ctypes.byref(st))
+    _check(rc)
+    return TT(out.value, dims)
+
+
+def _core_args(cores):
+    d = len(cores)
+    dtype = cores[0].dtype
+    if dtype not in (torch.float64, torch.float32):
+        raise FastTTError(EINVAL, "cores must be float64 or float32")
+    for G in cores:
+        if G.dtype != dtype or G.device.type != "cuda" or not G.is_contiguous() or G.dim() != 3:
+            raise FastTTError(EINVAL, "cores must be contiguous CUDA tensors (r0, n, r1) of one dtype")
+    dims = [int(G.shape[1]) for G in cores]
+    ranks = [int(cores[0].shape[0])] + [int(G.shape[2]) for G in cores]
+    ptrs = (ctypes.c_void_p * d)(*[G.data_ptr() for G in cores])
+    return d, dims, ranks, ptrs, (F64 if dtype == torch.float64 else F32), dtype
+
+
+def tt_eval_at(cores, idx, stream=None) -> torch.Tensor:
+    """a(i^e) = G_1[i_1] ... G_d[i_d] for every column of idx (d, m)."""
+    _require_cuda()
+    d, dims, ranks, ptrs, code, dtype = _core_args(cores)
+    idx = _dev(idx, torch.int32)
+    m = int(idx.shape[1])
+    out = torch.empty(m, dtype=dtype, device="cuda")
+    _check(_lib.tt_eval_at(d, _i64arr(dims), _i64arr(ranks), ptrs, code, m, ctypes.c_void_p(idx.data_ptr()),
+                           ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def tt_eval_backward(cores, idx, grad_out, grad_cores=None, recompute=False, stream=None):
+    """Adds dL/dG_k for L = sum_e grad_out[e] a(i^e) into grad_cores (zeros if None); returns them."""
+    _require_cuda()
+    d, dims, ranks, ptrs, code, dtype = _core_args(cores)
+    idx = _dev(idx, torch.int32)
+    grad_out = _dev(grad_out, dtype)
+    if grad_cores is None:
+        grad_cores = [torch.zeros_like(G) for G in cores]
+    gptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in grad_cores])
+    _check(_lib.tt_eval_backward(d, _i64arr(dims), _i64arr(ranks), ptrs, code, int(idx.shape[1]),
+                                 ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(grad_out.data_ptr()), gptrs,
+                                 1 if recompute else 0, _stream(stream)))
+    return grad_cores
+
+
+class TTEval(torch.autograd.Function):
+    """Differentiable entry evaluation: forward = tt_eval_at, backward = tt_eval_backward."""
+
+    @staticmethod
+    def forward(ctx, idx, recompute, *cores):
+        cores = [G.contiguous() for G in cores]
+        ctx.save_for_backward(idx, *cores)
+        ctx.recompute = bool(recompute)
+        return tt_eval_at(cores, idx)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        idx, *cores = ctx.saved_tensors
+        grads = tt_eval_backward(cores, idx, grad_out.contiguous(), recompute=ctx.recompute)
+        return (None, None, *grads)
+
+
+def tt_eval(cores, idx, recompute=False):
+    return TTEval.apply(idx, recompute, *cores)

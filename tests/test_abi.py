@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads and exports every function include/fasttt.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fasttt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_02721_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("fasttt_decompose", "tt_eval_at", "tt_eval_backward", "fasttt_tt_free",
+                     "fasttt_tt_ranks", "fasttt_tt_core", "fasttt_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_loads_and_matches_exports(lib):
+    from paper_1908_02721_gb300 import fasttt as F
+    assert sorted(F.EXPORTS) == _declared()
+    assert "sm_103a" in F.version()
+    o = F.Opts()
+    F._lib.fasttt_default_opts(ctypes.byref(o))
+    assert o.p == 0 and o.depar_values == 1 and o.max_rank == 0
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_1908_02721_gb300 import fasttt as F
+    # fasttt_opts: six ints then two int64; fasttt_stats ends with the kernel-class doubles
+    assert ctypes.sizeof(F.Opts) == 6 * 4 + 2 * 8
+    assert F.Stats.bytes_sort.offset + 8 == ctypes.sizeof(F.Stats)
+
+
+def test_calls_without_gpu_fail_loudly(lib):
+    import torch
+    from paper_1908_02721_gb300 import fasttt as F
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(F.FastTTError):
+        F.fasttt_decompose([[0, 1], [1, 0]], [1.0, 2.0], [2, 2], 0.0)
