@@ -499,6 +499,7 @@ int handle_error(const Error& e) {
 }
 
 }  // namespace
+
 }  // namespace fasttt
 
 using namespace fasttt;

@@ -260,3 +260,4 @@ int tt_eval_backward_impl(int d, const int64_t* dims, const int64_t* ranks, cons
 }
 
 }  // namespace fasttt
+
