@@ -194,6 +194,30 @@ int tt_eval_backward(int d, const int64_t* dims, const int64_t* ranks,
                      const void* d_grad_out, void* const* d_grad_cores, int recompute,
                      void* stream);
 
+/*
+ * tt_eval_backward_noalloc — for callers that cannot call cudaMalloc (or any
+ * allocator) on the device: for example code running inside a stream capture
+ * that must not allocate, a host framework that owns all device memory through
+ * its own pool, or an embedded runtime with a fixed memory budget.  The paper
+ * has no counterpart; this is a library-level service.
+ * Same arguments and result as tt_eval_backward with recompute = 0 (gradients
+ * ADDED into d_grad_cores).  Its scratch is a file-scope device array of
+ * FASTTT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits; the call allocates nothing.  The first call on a device
+ * looks up that array's device address (with the device current); make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other threads) race: serialise
+ * them.  The scratch holds, per resident warp, the left partial products
+ * (r_0 + ... + r_{d-1} values); one thread block of up to 8 warps must fit, so
+ * calls whose r_0 + ... + r_{d-1} exceeds 524,000 (FP64) or 1,048,000 (FP32) are
+ * rejected with FASTTT_ERANK and a message saying so; smaller sums only limit
+ * how many warps run at once.  Other errors as tt_eval_backward.
+ */
+#define FASTTT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int tt_eval_backward_noalloc(int d, const int64_t* dims, const int64_t* ranks,
+                             const void* const* d_cores, int dtype, int64_t m, const int32_t* d_idx,
+                             const void* d_grad_out, void* const* d_grad_cores, void* stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char* fasttt_last_error(void);
 

@@ -500,6 +500,8 @@ int handle_error(const Error& e) {
 
 }  // namespace
 
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 }  // namespace fasttt
 
 using namespace fasttt;

@@ -261,3 +261,46 @@ int tt_eval_backward_impl(int d, const int64_t* dims, const int64_t* ranks, cons
 
 }  // namespace fasttt
 
+namespace fasttt {
+
+// The adjoint with stored left partials, run in caller-provided device scratch:
+// the first 256 bytes hold the error flag, the rest the per-warp left partials.
+// The grid is sized so the partials fit.  Allocates no device memory.
+int tt_eval_backward_prealloc(int d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
+                              int dtype, int64_t m, const int32_t* idx, const void* gout, void* const* grads,
+                              void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  CoreArgs ca;
+  check_args(d, dims, ranks, cores, dtype, m, idx, ca);
+  if (!grads) fail(FASTTT_EINVAL, "null gradient array");
+  for (int k = 0; k < d; ++k) {
+    if (!grads[k]) fail(FASTTT_EINVAL, "null gradient core");
+    ca.grad[k] = grads[k];
+  }
+  if (m == 0) return FASTTT_OK;
+  if (!gout) fail(FASTTT_EINVAL, "null upstream gradient");
+  if (!scratch || scratch_bytes <= 256) fail(FASTTT_EINVAL, "no scratch");
+  unsigned* err = static_cast<unsigned*>(scratch);
+  const int rmax = max_rank_of(ca, d);
+  const size_t esz = (dtype == FASTTT_F64) ? 8 : 4;
+  const int64_t stride = ca.off[d];
+  size_t smem = 0;
+  int nw;
+  if (dtype == FASTTT_F64) nw = warps_for(backward_kernel<double>, rmax, 4, 8, &smem);
+  else nw = warps_for(backward_kernel<float>, rmax, 4, 4, &smem);
+  const int64_t fit_warps = (int64_t)((scratch_bytes - 256) / ((size_t)stride * esz));
+  const int64_t blocks = std::min<int64_t>(std::min<int64_t>(ceil_div(m, nw), (int64_t)kNumSMs * 32), fit_warps / nw);
+  if (blocks < 1) fail(FASTTT_ERANK, "sum of TT ranks too large for the fixed scratch");
+  FTT_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+  void* left = static_cast<unsigned char*>(scratch) + 256;
+  if (dtype == FASTTT_F64)
+    backward_kernel<double><<<(unsigned)blocks, nw * 32, smem, s>>>(d, ca, m, idx, (const double*)gout, 0,
+                                                                    (double*)left, stride, err, rmax);
+  else
+    backward_kernel<float><<<(unsigned)blocks, nw * 32, smem, s>>>(d, ca, m, idx, (const float*)gout, 0,
+                                                                   (float*)left, stride, err, rmax);
+  FTT_LAUNCH();
+  if (read_scalar(err, s)) fail(FASTTT_EINVAL, "index out of range");
+  return FASTTT_OK;
+}
+
+}  // namespace fasttt

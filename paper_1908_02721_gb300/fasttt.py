@@ -86,12 +86,15 @@ _lib.fasttt_tt_copy.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int
 _lib.tt_eval_at.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64, _P, _P, _P]
 _lib.tt_eval_backward.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64,
                                   _P, _P, ctypes.POINTER(_P), ctypes.c_int, _P]
+_lib.tt_eval_backward_noalloc.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int,
+                                          ctypes.c_int64, _P, _P, ctypes.POINTER(_P), _P]
 _lib.fasttt_last_error.restype = ctypes.c_char_p
 _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
 
 EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_tt_stats", "fasttt_tt_ranks",
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
+           "tt_eval_backward_noalloc",
            "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after"]
 
 
@@ -250,6 +253,25 @@ def tt_eval_backward(cores, idx, grad_out, grad_cores=None, recompute=False, str
     _check(_lib.tt_eval_backward(d, _i64arr(dims), _i64arr(ranks), ptrs, code, int(idx.shape[1]),
                                  ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(grad_out.data_ptr()), gptrs,
                                  1 if recompute else 0, _stream(stream)))
+    return grad_cores
+
+
+def tt_eval_backward_noalloc(cores, idx, grad_out, grad_cores, stream=None):
+    """tt_eval_backward for callers that cannot allocate device memory: the
+    library works in its fixed, process-lifetime scratch array instead.  The
+    caller provides every input and the (pre-allocated) gradient cores, which
+    receive the gradient ADDED to their contents.  Calls sharing the scratch
+    must not overlap on the GPU."""
+    _require_cuda()
+    d, dims, ranks, ptrs, code, dtype = _core_args(cores)
+    if idx.device.type != "cuda" or idx.dtype != torch.int32 or not idx.is_contiguous():
+        raise FastTTError(EINVAL, "idx must be a contiguous int32 CUDA tensor")
+    if grad_out.device.type != "cuda" or grad_out.dtype != dtype or not grad_out.is_contiguous():
+        raise FastTTError(EINVAL, "grad_out must be a contiguous CUDA tensor of the cores' dtype")
+    gptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in grad_cores])
+    _check(_lib.tt_eval_backward_noalloc(d, _i64arr(dims), _i64arr(ranks), ptrs, code, int(idx.shape[1]),
+                                         ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(grad_out.data_ptr()),
+                                         gptrs, _stream(stream)))
     return grad_cores
 
 
