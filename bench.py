@@ -196,31 +196,9 @@ def run_ours(args):
     value = w.nnz * world / (ms / 1e3)
 
     # e2e through the same C-ABI call from pinned host memory
-    idx_h = torch.from_numpy(w.idx).pin_memory()
-    vals_h = torch.from_numpy(w.vals).pin_memory()
-    e2e_ms, d2h = [], 0
-    for i in range(args.steps + 1):
-        barrier()
-        t = time.perf_counter()
-        di = idx_h.to(dev, non_blocking=True)
-        dv = vals_h.to(dev, non_blocking=True)
-        tt = F.fasttt_decompose(di, dv, w.dims, w.eps)
-        host = [torch.empty(tt.ranks[k - 1] * w.dims[k - 1] * tt.ranks[k], dtype=torch.float64).pin_memory()
-                for k in range(1, w.d + 1)] if i == 0 else host
-        for k in range(1, w.d + 1):
-            F._check(F._lib.fasttt_tt_copy(tt._h, F.ARR["core"], k, host[k - 1].data_ptr(), host[k - 1].numel()))
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t
-        d2h = sum(h.numel() * 8 for h in host)
-        tt.free()
-        if i > 0:                      # the first pass pins the host buffers
-            e2e_ms.append(el * 1e3)
-    e2e = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e = float(t.item())
-
+    e2e_line = None
+    if not args.no_e2e:
+        e2e_line = _e2e(args, w, F, dev, barrier, world)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
@@ -248,16 +226,48 @@ def run_ours(args):
                        "rt": st["rt"], "beta": [st["beta_r"], st["beta_c"]],
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}"},
-            "e2e": {"value": w.nnz * world / (e2e / 1e3), "unit": "nnz/s",
-                    "h2d_bytes_per_step": int(w.idx.nbytes + w.vals.nbytes), "d2h_bytes_per_step": int(d2h)},
+            "e2e": e2e_line,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm",
-                                              "ms_jacobi", "ms_sort")},
+                                              "ms_jacobi", "ms_jacobi32", "ms_sort")},
+            "jacobi_sweeps": st["jacobi_sweeps"],
             "wall_s": wall, "peaks_source": src}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _e2e(args, w, F, dev, barrier, world):
+    """Same call from pinned host buffers: H2D of the COO input and D2H of every core timed."""
+    import torch
+    idx_h = torch.from_numpy(w.idx).pin_memory()
+    vals_h = torch.from_numpy(w.vals).pin_memory()
+    e2e_ms, d2h, host = [], 0, None
+    for i in range(args.steps + 1):
+        barrier()
+        t = time.perf_counter()
+        di = idx_h.to(dev, non_blocking=True)
+        dv = vals_h.to(dev, non_blocking=True)
+        tt = F.fasttt_decompose(di, dv, w.dims, w.eps)
+        if host is None:
+            host = [torch.empty(tt.ranks[k - 1] * w.dims[k - 1] * tt.ranks[k], dtype=torch.float64).pin_memory()
+                    for k in range(1, w.d + 1)]
+        for k in range(1, w.d + 1):
+            F._check(F._lib.fasttt_tt_copy(tt._h, F.ARR["core"], k, host[k - 1].data_ptr(), host[k - 1].numel()))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        d2h = sum(h.numel() * 8 for h in host)
+        tt.free()
+        if i > 0:                      # the first pass also pins the host buffers
+            e2e_ms.append(el * 1e3)
+    e2e = sum(e2e_ms) / len(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e = float(t.item())
+    return {"value": w.nnz * world / (e2e / 1e3), "unit": "nnz/s",
+            "h2d_bytes_per_step": int(w.idx.nbytes + w.vals.nbytes), "d2h_bytes_per_step": int(d2h)}
 
 
 def main():
@@ -267,6 +277,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

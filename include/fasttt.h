@@ -94,6 +94,7 @@ typedef struct fasttt_stats {
    * (2MNK flops), Jacobi sweeps (dot products + applied rotations, flops) and
    * radix-sort passes (key/value bytes moved) */
   double ms_gemm, flop_gemm, ms_jacobi, flop_jacobi, ms_sort, bytes_sort;
+  double ms_jacobi32, flop_jacobi32; /* the FP32 Jacobi sweeps that precondition large eigenproblems */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */

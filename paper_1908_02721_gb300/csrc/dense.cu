@@ -37,7 +37,9 @@ constexpr int kDirectMax = 512;
 __global__ void __launch_bounds__(256)
     gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A, int64_t sai,
                     int64_t sak, const double* __restrict__ B, int64_t sbk, int64_t sbj, double beta,
-                    double* __restrict__ C, int64_t sci, int64_t scj) {
+                    double* __restrict__ C, int64_t sci, int64_t scj, bool sym) {
+  // sym: C is symmetric; tiles strictly below the diagonal are skipped (mirrored later)
+  if (sym && (int64_t)blockIdx.x * kTile >= ((int64_t)blockIdx.y + 1) * kTile) return;
   __shared__ double As[kTileK][kTile + 1];
   __shared__ double Bs[kTileK][kTile + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -109,8 +111,10 @@ __global__ void identity_kernel(double* V, int64_t n) {
 }
 
 // Block-wide sum of three values (256 threads).
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
-  __shared__ double red[3][8];
+template <typename T>
+__device__ __forceinline__ void block_sum3(T& a, T& b, T& c) {
+  __shared__ T red[3][8];
+  __syncthreads();  // earlier readers of red are done
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
@@ -121,7 +125,7 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
   if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double x = 0, y = 0, z = 0;
+    T x = 0, y = 0, z = 0;
     for (int w = 0; w < 8; ++w) { x += red[0][w]; y += red[1][w]; z += red[2][w]; }
     red[0][0] = x; red[1][0] = y; red[2][0] = z;
   }
@@ -129,60 +133,223 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
   a = red[0][0]; b = red[1][0]; c = red[2][0];
 }
 
-// One round of the circle schedule: block i rotates pair i.
-__global__ void __launch_bounds__(256) jacobi_round_kernel(double* A, int64_t m, int64_t lda, double* V,
-                                                           int64_t nv, int64_t ldv, int n, int n2, int round,
-                                                           double tol, double small2, unsigned* rotations) {
-  const int i = blockIdx.x;
+template <bool kCoherent, typename T>
+__device__ __forceinline__ T ld(const T* p) {
+  if constexpr (kCoherent) return __ldcg(p);  // bypass L1: other blocks wrote it this launch
+  else return *p;
+}
+
+// Rotate pair i of round `round` of the circle schedule (whole block).
+template <bool kCoherent, typename T>
+__device__ __forceinline__ void jacobi_pair(T* A, int64_t m, int64_t lda, T* V, int64_t nv, int64_t ldv, int n,
+                                            int n2, int round, int i, T tol, T small2, unsigned* rotations) {
   int p, q;
   if (i == 0) { p = round; q = n2 - 1; }
   else { p = (round + i) % (n2 - 1); q = (round - i + (n2 - 1)) % (n2 - 1); }
   if (p > q) { const int t = p; p = q; q = t; }
   if (q >= n) return;  // the dummy player of an odd n
-  double* ap = A + (int64_t)p * lda;
-  double* aq = A + (int64_t)q * lda;
-  double alpha = 0.0, beta = 0.0, gamma = 0.0;
+  T* ap = A + (int64_t)p * lda;
+  T* aq = A + (int64_t)q * lda;
+  T alpha = 0, beta = 0, gamma = 0;
   for (int64_t e = threadIdx.x; e < m; e += blockDim.x) {
-    const double x = ap[e], y = aq[e];
+    const T x = ld<kCoherent>(ap + e), y = ld<kCoherent>(aq + e);
     alpha = fma(x, x, alpha);
     beta = fma(y, y, beta);
     gamma = fma(x, y, gamma);
   }
-  block_sum3(alpha, beta, gamma);
+  block_sum3<T>(alpha, beta, gamma);
   // columns at roundoff level relative to ||A||_F are treated as zero
-  if (gamma == 0.0 || alpha <= small2 || beta <= small2) return;
+  if (gamma == T(0) || alpha <= small2 || beta <= small2) return;
   if (fabs(gamma) <= tol * sqrt(alpha) * sqrt(beta)) return;
-  const double zeta = (beta - alpha) / (2.0 * gamma);
-  const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-  const double c = 1.0 / sqrt(fma(t, t, 1.0));
-  const double s = c * t;
+  const T zeta = (beta - alpha) / (T(2) * gamma);
+  const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+  const T c = T(1) / sqrt(fma(t, t, T(1)));
+  const T sn = c * t;
   if (threadIdx.x == 0) atomicAdd(rotations, 1u);
   for (int64_t e = threadIdx.x; e < m; e += blockDim.x) {
-    const double x = ap[e], y = aq[e];
-    ap[e] = c * x - s * y;
-    aq[e] = s * x + c * y;
+    const T x = ld<kCoherent>(ap + e), y = ld<kCoherent>(aq + e);
+    ap[e] = c * x - sn * y;
+    aq[e] = sn * x + c * y;
   }
   if (V) {
-    double* vp = V + (int64_t)p * ldv;
-    double* vq = V + (int64_t)q * ldv;
+    T* vp = V + (int64_t)p * ldv;
+    T* vq = V + (int64_t)q * ldv;
     for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
-      const double x = vp[e], y = vq[e];
-      vp[e] = c * x - s * y;
-      vq[e] = s * x + c * y;
+      const T x = ld<kCoherent>(vp + e), y = ld<kCoherent>(vq + e);
+      vp[e] = c * x - sn * y;
+      vq[e] = sn * x + c * y;
     }
   }
 }
 
-__global__ void col_norms_kernel(const double* A, int64_t m, int64_t lda, int n, double* out) {
+// One round of the circle schedule per launch: block i rotates pair i.
+template <typename T>
+__global__ void __launch_bounds__(256) jacobi_round_kernel(T* A, int64_t m, int64_t lda, T* V, int64_t nv,
+                                                           int64_t ldv, int n, int n2, int round, T tol, T small2,
+                                                           unsigned* rotations) {
+  jacobi_pair<false, T>(A, m, lda, V, nv, ldv, n, n2, round, blockIdx.x, tol, small2, rotations);
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  bar[0]
+// counts arrivals, bar[1] is the generation, bar[2] an error flag.  The wait is
+// bounded: after kBarrierSpins polls the block raises the error flag and every
+// block leaves the kernel at its next barrier.
+constexpr long long kBarrierSpins = 1ll << 24;
+constexpr int64_t kWarpPairMax = 16384;
+
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen) {
+  __shared__ int ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* verr = bar + 2;
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == gen) {
+        if (*verr) { ok = 0; break; }
+        if (++it > kBarrierSpins) { atomicOr(bar + 2, 1u); ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    if (*verr) ok = 0;
+    __threadfence();
+  }
+  __syncthreads();
+  ++gen;
+  return ok != 0;
+}
+
+// (a, b) <- (c a - s b, s a + c b) over n elements, U loads per lane in flight
+template <typename T, int U>
+__device__ __forceinline__ void rotate_cols_warp(T* a, T* b, int64_t n, T c, T sn, int lane) {
+  for (int64_t e0 = 0; e0 < n; e0 += 32 * U) {
+    T x[U], y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = e0 + u * 32 + lane;
+      x[u] = (e < n) ? __ldcg(a + e) : T(0);
+      y[u] = (e < n) ? __ldcg(b + e) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = e0 + u * 32 + lane;
+      if (e < n) {
+        a[e] = c * x[u] - sn * y[u];
+        b[e] = sn * x[u] + c * y[u];
+      }
+    }
+  }
+}
+
+// Rotate pair i of round `round` with one warp (lane-strided columns, shuffle
+// reductions, all lanes hold the sums).  Loads bypass L1: the columns were
+// written by other warps earlier in the same launch.
+template <typename T>
+__device__ __forceinline__ void jacobi_pair_warp(T* A, int64_t m, int64_t lda, T* V, int64_t nv, int64_t ldv,
+                                                 int n, int n2, int round, int i, T tol, T small2,
+                                                 unsigned* rotations, int lane) {
+  int p, q;
+  if (i == 0) { p = round; q = n2 - 1; }
+  else { p = (round + i) % (n2 - 1); q = (round - i + (n2 - 1)) % (n2 - 1); }
+  if (p > q) { const int t = p; p = q; q = t; }
+  if (q >= n) return;
+  T* ap = A + (int64_t)p * lda;
+  T* aq = A + (int64_t)q * lda;
+  T alpha = 0, beta = 0, gamma = 0;
+  // 8 independent loads per lane in flight per step (the column lives in L2)
+  constexpr int U = 8;
+  for (int64_t e0 = 0; e0 < m; e0 += 32 * U) {
+    T x[U], y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = e0 + u * 32 + lane;
+      x[u] = (e < m) ? __ldcg(ap + e) : T(0);
+      y[u] = (e < m) ? __ldcg(aq + e) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      alpha = fma(x[u], x[u], alpha);
+      beta = fma(y[u], y[u], beta);
+      gamma = fma(x[u], y[u], gamma);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+    beta += __shfl_xor_sync(0xffffffffu, beta, o);
+    gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+  }
+  if (gamma == T(0) || alpha <= small2 || beta <= small2) return;
+  if (fabs(gamma) <= tol * sqrt(alpha) * sqrt(beta)) return;
+  const T zeta = (beta - alpha) / (T(2) * gamma);
+  const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+  const T c = T(1) / sqrt(fma(t, t, T(1)));
+  const T sn = c * t;
+  if (lane == 0) atomicAdd(rotations, 1u);
+  rotate_cols_warp<T, U>(ap, aq, m, c, sn, lane);
+  if (V) rotate_cols_warp<T, U>(V + (int64_t)p * ldv, V + (int64_t)q * ldv, nv, c, sn, lane);
+}
+
+// A whole sweep in one cooperative launch, one warp per pair.
+template <typename T>
+__global__ void __launch_bounds__(256) jacobi_sweep_warp_kernel(T* A, int64_t m, int64_t lda, T* V, int64_t nv,
+                                                                int64_t ldv, int n, int n2, T tol, T small2,
+                                                                unsigned* rotations, unsigned* bar) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  unsigned gen = 0;
+  for (int round = 0; round < n2 - 1; ++round) {
+    for (int i = gw; i < n2 / 2; i += nw)
+      jacobi_pair_warp<T>(A, m, lda, V, nv, ldv, n, n2, round, i, tol, small2, rotations, lane);
+    if (!grid_barrier(bar, gridDim.x, gen)) return;
+  }
+}
+
+// A whole sweep (all n2-1 rounds) in one cooperative launch; blocks take pairs
+// grid-stride and meet at a grid barrier after every round.
+template <typename T>
+__global__ void __launch_bounds__(256) jacobi_sweep_kernel(T* A, int64_t m, int64_t lda, T* V, int64_t nv,
+                                                           int64_t ldv, int n, int n2, T tol, T small2,
+                                                           unsigned* rotations, unsigned* bar) {
+  unsigned gen = 0;
+  for (int round = 0; round < n2 - 1; ++round) {
+    for (int i = blockIdx.x; i < n2 / 2; i += gridDim.x)
+      jacobi_pair<true, T>(A, m, lda, V, nv, ldv, n, n2, round, i, tol, small2, rotations);
+    if (!grid_barrier(bar, gridDim.x, gen)) return;
+  }
+}
+
+template <typename T>
+__global__ void col_norms_kernel(const T* A, int64_t m, int64_t lda, int n, T* out) {
   const int j = blockIdx.x;
   if (j >= n) return;
-  const double* a = A + (int64_t)j * lda;
-  double s = 0.0, d1 = 0.0, d2 = 0.0;
+  const T* a = A + (int64_t)j * lda;
+  T s = 0, d1 = 0, d2 = 0;
   for (int64_t e = threadIdx.x; e < m; e += blockDim.x) s = fma(a[e], a[e], s);
-  block_sum3(s, d1, d2);
+  block_sum3<T>(s, d1, d2);
   if (threadIdx.x == 0) out[j] = sqrt(s);
 }
 
+__global__ void to_f32_kernel(const double* a, int64_t n, float* b) { GRID_STRIDE(i, n) b[i] = (float)a[i]; }
+__global__ void to_f64_kernel(const float* a, int64_t n, double* b) { GRID_STRIDE(i, n) b[i] = (double)a[i]; }
+__global__ void identity_f32_kernel(float* V, int64_t n) {
+  GRID_STRIDE(i, n * n) V[i] = ((i / n) == (i % n)) ? 1.0f : 0.0f;
+}
+// C (n x n, row-major): lower triangle := upper triangle
+__global__ void mirror_upper_kernel(double* C, int64_t n) {
+  GRID_STRIDE(e, n * n) {
+    const int64_t i = e / n, j = e % n;
+    if (i > j) C[e] = C[j * n + i];
+  }
+}
 // out (rows x r, row-major): out[i, c] = src[perm[c] * ld + i] * scale[c]
 __global__ void gather_cols_kernel(const double* src, int64_t ld, int64_t rows, const int32_t* perm,
                                    const double* scale, int64_t r, double* out) {
@@ -202,57 +369,218 @@ __global__ void gather_rows_kernel(const double* src, int64_t ld, int64_t cols, 
 }
 
 // One-sided Jacobi on the n columns (length m) of A; V (nv x n) receives the
-// same rotations.  Returns the number of sweeps.
-int64_t jacobi(double* A, int64_t m, int64_t lda, int n, double* V, int64_t nv, int64_t ldv,
-               int64_t max_sweeps, cudaStream_t s) {
+// same rotations.  Returns the number of sweeps; -1 if the bound was hit.
+template <typename T>
+int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ldv, int64_t max_sweeps,
+               cudaStream_t s) {
   if (n < 2) return 0;
   const int n2 = n + (n & 1);
-  const double tol = sqrt((double)m) * 0x1p-52;
-  double small2;
+  const bool f64 = sizeof(T) == 8;
+  const T tol = (T)(sqrt((double)m) * (f64 ? 0x1p-52 : 0x1p-23));
+  T small2;
   {
-    DBuf<double> norms(n, s);
-    col_norms_kernel<<<n, 256, 0, s>>>(A, m, lda, n, norms.get());
+    DBuf<T> norms(n, s);
+    col_norms_kernel<T><<<n, 256, 0, s>>>(A, m, lda, n, norms.get());
     FTT_LAUNCH();
-    std::vector<double> h(n);
-    FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    std::vector<T> h(n);
+    FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(T) * n, cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
     double f2 = 0.0;
-    for (double x : h) f2 += x * x;
-    small2 = f2 * 0x1p-100;  // (2^-50 ||A||_F)^2
+    for (T x : h) f2 += (double)x * (double)x;
+    small2 = (T)(f2 * (f64 ? 0x1p-100 : 0x1p-42));  // (2^-50 or 2^-21 of ||A||_F)^2
   }
-  DBuf<unsigned> rot(1, s);
+  DBuf<unsigned> rot(4, s);  // [0] rotations, [1..3] grid barrier
   const double pairs = 0.5 * (double)n * (double)(n - 1);
+  // cooperative grid: every block resident at once (bounded by the occupancy)
+  int per_sm = 0, coop = 0, dev = 0;
+  FTT_CUDA(cudaGetDevice(&dev));
+  FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  // columns up to kWarpPairMax long: one warp per pair; longer: one block per pair
+  const bool warp_pairs = (m <= kWarpPairMax && nv <= kWarpPairMax);
+  void* sweep_fn = warp_pairs ? (void*)jacobi_sweep_warp_kernel<T> : (void*)jacobi_sweep_kernel<T>;
+  FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn, 256, 0));
+  int sms = 0;
+  FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int units_per_block = warp_pairs ? 8 : 1;
+  const int coop_blocks = std::min((n2 / 2 + units_per_block - 1) / units_per_block, per_sm * sms);
+  bool use_coop = coop && coop_blocks >= 1 && n2 / 2 > 1;
   for (int64_t sweep = 1; sweep <= max_sweeps; ++sweep) {
-    FTT_CUDA(cudaMemsetAsync(rot.get(), 0, sizeof(unsigned), s));
+    FTT_CUDA(cudaMemsetAsync(rot.get(), 0, 4 * sizeof(unsigned), s));
     KClock clk;
-    kclock_begin(clk, KC_JACOBI, s);
-    for (int round = 0; round < n2 - 1; ++round) {
-      jacobi_round_kernel<<<n2 / 2, 256, 0, s>>>(A, m, lda, V, nv, ldv, n, n2, round, tol, small2, rot.get());
+    kclock_begin(clk, f64 ? KC_JACOBI : KC_JACOBI32, s);
+    bool done = false;
+    if (use_coop) {
+      unsigned* rp = rot.get();
+      unsigned* bp = rot.get() + 1;
+      void* args[] = {(void*)&A, (void*)&m, (void*)&lda, (void*)&V, (void*)&nv, (void*)&ldv, (void*)&n,
+                      (void*)&n2, (void*)&tol, (void*)&small2, (void*)&rp, (void*)&bp};
+      cudaError_t e = cudaLaunchCooperativeKernel(sweep_fn, dim3(coop_blocks), dim3(256), args, 0, s);
+      if (e == cudaSuccess) {
+        FTT_LAUNCH();
+        unsigned h[4];
+        FTT_CUDA(cudaMemcpyAsync(h, rot.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+        FTT_CUDA(cudaStreamSynchronize(s));
+        if (h[3] == 0) done = true;       // no barrier timed out
+        else use_coop = false;            // redo this sweep round by round
+      } else {
+        cudaGetLastError();
+        use_coop = false;
+      }
+      if (!done) FTT_CUDA(cudaMemsetAsync(rot.get(), 0, 4 * sizeof(unsigned), s));
     }
-    note_launches(n2 - 2);
-    FTT_LAUNCH();
+    if (!done) {
+      for (int round = 0; round < n2 - 1; ++round) {
+        jacobi_round_kernel<T><<<n2 / 2, 256, 0, s>>>(A, m, lda, V, nv, ldv, n, n2, round, tol, small2, rot.get());
+      }
+      note_launches(n2 - 2);
+      FTT_LAUNCH();
+    }
     const unsigned rots = read_scalar(rot.get(), s);
     // every pair: three dot products (6m flops); every rotation: 6m + 6nv flops
     kclock_end(clk, pairs * 6.0 * (double)m + (double)rots * 6.0 * (double)(m + (V ? nv : 0)), s);
     if (rots == 0) return sweep;
   }
-  fail(FASTTT_ETIMEOUT, "Jacobi SVD did not converge within the sweep bound");
+  return -1;
+}
+
+int64_t jacobi_f64(double* A, int64_t m, int64_t lda, int n, double* V, int64_t nv, int64_t ldv,
+                   int64_t max_sweeps, cudaStream_t s) {
+  const int64_t sw = jacobi<double>(A, m, lda, n, V, nv, ldv, max_sweeps, s);
+  if (sw < 0) fail(FASTTT_ETIMEOUT, "Jacobi SVD did not converge within the sweep bound");
+  return sw;
+}
+
+// Sum of squares of M (n x n, row-major) with `diag` subtracted from the
+// diagonal (diag may be null); per-block partials, summed on the host in order.
+__global__ void __launch_bounds__(256) sumsq_offdiag_kernel(const double* M, const double* diag, int64_t n,
+                                                            double* partial) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    double x = M[e];
+    if (diag && e / n == e % n) x -= diag[e / n];
+    acc = fma(x, x, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// R <- I - R (R holds X^T X on entry)
+__global__ void i_minus_kernel(double* R, int64_t n) {
+  GRID_STRIDE(e, n * n) R[e] = ((e / n) == (e % n) ? 1.0 : 0.0) - R[e];
+}
+
+// lambda_i = s_ii / (1 - r_ii)
+__global__ void oa_lambda_kernel(const double* S, const double* R, int64_t n, double* lam) {
+  GRID_STRIDE(i, n) lam[i] = S[i * n + i] / (1.0 - R[i * n + i]);
+}
+
+// The correction of the refinement step: e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)
+// for |lambda_j - lambda_i| > delta, e_ij = r_ij / 2 otherwise (clusters, diagonal).
+__global__ void oa_correction_kernel(const double* S, const double* R, const double* lam, double delta, int64_t n,
+                                     double* E) {
+  GRID_STRIDE(e, n * n) {
+    const int64_t i = e / n, j = e % n;
+    const double d = lam[j] - lam[i];
+    E[e] = (i != j && fabs(d) > delta) ? (S[e] + lam[j] * R[e]) / d : 0.5 * R[e];
+  }
+}
+
+double sumsq(const double* M, const double* diag, int64_t n, cudaStream_t s) {
+  const int blocks = 2 * kNumSMs;
+  DBuf<double> part(blocks, s);
+  sumsq_offdiag_kernel<<<blocks, 256, 0, s>>>(M, diag, n, part.get());
+  FTT_LAUNCH();
+  std::vector<double> h(blocks);
+  FTT_CUDA(cudaMemcpyAsync(h.data(), part.get(), sizeof(double) * blocks, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaStreamSynchronize(s));
+  double t = 0.0;
+  for (double x : h) t += x;
+  return t;
+}
+
+// Eigen-decomposition of a symmetric positive semi-definite n x n matrix G
+// (FP64, row-major; left intact).  FP32 one-sided Jacobi from V = I gives
+// approximate eigenvectors X (orthonormal to ~1e-7); then the iterative
+// refinement for symmetric eigendecompositions of Ogita & Aishima (Japan J.
+// Indust. Appl. Math. 35, 2018) in FP64, which needs only products:
+//   R = I - X^T X,  S = X^T G X,  lambda_i = s_ii / (1 - r_ii),
+//   delta = 2 (||S - diag(lambda)|| + ||G|| ||R||)   (Frobenius norms, >= 2-norms),
+//   E_ij as in oa_correction_kernel,  X <- X + X E,
+// repeated until ||R|| and ||S - diag(lambda)|| / ||G|| are at rounding level.
+// V (column-major: column j = eigenvector j, i.e. row-major X^T) and the
+// eigenvalues (host) are returned.  Returns the FP32 sweeps.
+int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps,
+                        cudaStream_t s) {
+  const int64_t nn = (int64_t)n * n;
+  int64_t sweeps;
+  {
+    DBuf<float> G32(nn, s), V32(nn, s);
+    to_f32_kernel<<<grid_for(nn), 256, 0, s>>>(G, nn, G32.get());
+    FTT_LAUNCH();
+    identity_f32_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), n);
+    FTT_LAUNCH();
+    sweeps = jacobi<float>(G32.get(), n, n, n, V32.get(), n, n, max_sweeps, s);  // a starting point only
+    to_f64_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), nn, V);
+    FTT_LAUNCH();
+  }
+  const double g2 = sumsq(G, nullptr, n, s);
+  const double gF = sqrt(g2);
+  DBuf<double> R(nn, s), W(nn, s), S(nn, s), lam(n, s);
+  lam_out.assign(n, 0.0);
+  for (int it = 0; it < 6; ++it) {
+    // X^T is V's memory (row-major, row j = eigenvector j)
+    gemm_f64(n, n, n, 1.0, V, n, 1, V, 1, n, 0.0, R.get(), n, 1, s, true);           // X^T X
+    i_minus_kernel<<<grid_for(nn), 256, 0, s>>>(R.get(), n);
+    FTT_LAUNCH();
+    gemm_f64(n, n, n, 1.0, V, n, 1, G, n, 1, 0.0, W.get(), n, 1, s);                 // W = X^T G (row j = (G x_j)^T)
+    gemm_f64(n, n, n, 1.0, V, n, 1, W.get(), 1, n, 0.0, S.get(), n, 1, s, true);     // S = X^T G X
+    oa_lambda_kernel<<<grid_for(n), 256, 0, s>>>(S.get(), R.get(), n, lam.get());
+    FTT_LAUNCH();
+    const double offS = sqrt(sumsq(S.get(), lam.get(), n, s));
+    const double rF = sqrt(sumsq(R.get(), nullptr, n, s));
+    FTT_CUDA(cudaMemcpyAsync(lam_out.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(offS) || !std::isfinite(rF)) fail(FASTTT_ENUMERIC, "non-finite eigen refinement");
+    const double tiny = 4.0 * (double)n * 0x1p-53;
+    if (rF <= tiny && offS <= tiny * gF) break;   // X orthonormal and S diagonal to rounding
+    const double delta = 2.0 * (offS + gF * rF);
+    oa_correction_kernel<<<grid_for(nn), 256, 0, s>>>(S.get(), R.get(), lam.get(), delta, n, W.get());  // W <- E
+    FTT_LAUNCH();
+    // X <- X + X E, in X^T layout: X^T <- X^T + E^T X^T
+    FTT_CUDA(cudaMemcpyAsync(S.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    gemm_f64(n, n, n, 1.0, W.get(), 1, n, S.get(), n, 1, 1.0, V, n, 1, s);
+  }
+  return sweeps;
 }
 
 }  // namespace
 
 void gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
               const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
-              cudaStream_t s) {
+              cudaStream_t s, bool sym) {
   if (M <= 0 || N <= 0) return;
+  if (sym && (M != N || sci != N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
   const int64_t gx = ceil_div(M, kTile), gy = ceil_div(N, kTile);
   if (gy > 65535) fail(FASTTT_ERANK, "GEMM: N too large");
   dim3 grid((unsigned)gx, (unsigned)gy);
   KClock clk;
   kclock_begin(clk, KC_GEMM, s);
-  gemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj);
+  gemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, sym);
   FTT_LAUNCH();
-  kclock_end(clk, 2.0 * (double)M * (double)N * (double)K, s);
+  // algorithmic flops: the full product (a symmetric product's mirrored half is not counted twice)
+  kclock_end(clk, (sym ? 1.0 : 2.0) * (double)M * (double)N * (double)K + (sym ? (double)M * K : 0.0), s);
+  if (sym) {
+    mirror_upper_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M);
+    FTT_LAUNCH();
+  }
 }
 
 void transpose_f64(const double* src, int64_t rows, int64_t cols, double* dst, cudaStream_t s) {
@@ -283,24 +611,27 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
   } else {
     A = DBuf<double>((size_t)n * n, s);
     if (tall)  // G = Z^T Z
-      gemm_f64(N, N, M, 1.0, Z, 1, N, Z, N, 1, 0.0, A.get(), N, 1, s);
+      gemm_f64(N, N, M, 1.0, Z, 1, N, Z, N, 1, 0.0, A.get(), N, 1, s, true);
     else       // G = Z Z^T
-      gemm_f64(M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, A.get(), M, 1, s);
+      gemm_f64(M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, A.get(), M, 1, s, true);
     m_len = n;
     lda = n;
   }
   DBuf<double> V((size_t)n * n, s);
-  identity_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(V.get(), n);
-  FTT_LAUNCH();
-  out.sweeps = jacobi(A.get(), m_len, lda, n, V.get(), n, n, max_sweeps, s);
-  DBuf<double> norms(n, s);
-  col_norms_kernel<<<n, 256, 0, s>>>(A.get(), m_len, lda, n, norms.get());
-  FTT_LAUNCH();
   std::vector<double> h(n);
-  FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-  FTT_CUDA(cudaStreamSynchronize(s));
-  if (!direct)
-    for (auto& x : h) x = sqrt(x);  // eigenvalues of the Gram -> singular values
+  if (direct) {
+    identity_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(V.get(), n);
+    FTT_LAUNCH();
+    out.sweeps = jacobi_f64(A.get(), m_len, lda, n, V.get(), n, n, max_sweeps, s);
+    DBuf<double> norms(n, s);
+    col_norms_kernel<double><<<n, 256, 0, s>>>(A.get(), m_len, lda, n, norms.get());
+    FTT_LAUNCH();
+    FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+  } else {
+    out.sweeps = sym_eig_refined(A.get(), n, V.get(), h, max_sweeps, s);
+    for (auto& x : h) x = sqrt(std::max(x, 0.0));  // eigenvalues of the Gram -> singular values
+  }
   for (double x : h)
     if (!std::isfinite(x)) fail(FASTTT_ENUMERIC, "non-finite singular value");
   std::vector<int32_t> perm(n);

@@ -8,11 +8,13 @@
 
 namespace fasttt {
 
-// C(i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j) with element strides:
+// C(i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j) with element strides.
+// sym = true: C is known to be symmetric (square, row-major); only tiles on or
+// above the diagonal are computed and the lower triangle is mirrored.
 // A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj], C(i,j) = C[i*sci + j*scj].
 void gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
               const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
-              cudaStream_t s);
+              cudaStream_t s, bool sym = false);
 
 // dst (cols x rows, row-major) = transpose of src (rows x cols, row-major)
 void transpose_f64(const double* src, int64_t rows, int64_t cols, double* dst, cudaStream_t s);

@@ -259,6 +259,8 @@ void finish_stats(fasttt_stats& st, int64_t launches0) {
   st.flop_jacobi = work[KC_JACOBI];
   st.ms_sort = ms[KC_SORT];
   st.bytes_sort = work[KC_SORT];
+  st.ms_jacobi32 = ms[KC_JACOBI32];
+  st.flop_jacobi32 = work[KC_JACOBI32];
   kclock_reset();
   st.launches = launch_count() - launches0;
 }
@@ -332,6 +334,15 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   std::vector<int64_t> r(d + 1, 1);
   for (int k = 0; k <= d; ++k) r[k] = g.rt[k];
   std::vector<DBuf<double>> G(d + 1);  // 1-based dense cores
+  DBuf<double> UC;                      // G_p = Q_S UC while G[p] is empty (p < d)
+  auto expand_Q_S = [&](const double* U, int64_t rr) {
+    DBuf<double> X((size_t)g.mid_rows * rr, s);
+    FTT_CUDA(cudaMemsetAsync(X.get(), 0, X.bytes(), s));
+    expand_rows_kernel<<<grid_for(dp.rows.nz * rr), 256, 0, s>>>(
+        dp.rows.ids.get(), dp.rows.cls.get(), dp.rows.pref.get(), dp.rows.lam.get(), dp.rows.nz, U, rr, X.get());
+    FTT_LAUNCH();
+    return X;
+  };
   double err2 = 0.0;
   auto record = [&](int bond, const SvdOut& sv, double dl) {
     const double e2 = tail2(sv.sigma_all, sv.r);
@@ -359,13 +370,14 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
     C.reset();
     const double e2 = record(bond, sv, dl);
     const int64_t rr = sv.r;
-    // U_X = Q_S U_C (mid_rows x rr), V-side: Sigma V_C^T Q_T (rr x mid_cols)
-    DBuf<double> UX((size_t)g.mid_rows * rr, s);
-    FTT_CUDA(cudaMemsetAsync(UX.get(), 0, UX.bytes(), s));
-    expand_rows_kernel<<<grid_for(dp.rows.nz * rr), 256, 0, s>>>(
-        dp.rows.ids.get(), dp.rows.cls.get(), dp.rows.pref.get(), dp.rows.lam.get(), dp.rows.nz, sv.U.get(), rr,
-        UX.get());
-    FTT_LAUNCH();
+    // U_X = Q_S U_C (mid_rows x rr), V-side: Sigma V_C^T Q_T (rr x mid_cols).  For p < d
+    // G_p stays factored as Q_S U_C until the QR sweep multiplies R^T into it.
+    DBuf<double> UX;
+    if (p < d) {
+      UC = std::move(sv.U);
+    } else {
+      UX = expand_Q_S(sv.U.get(), rr);
+    }
     DBuf<double> SW((size_t)rr * g.mid_cols, s);
     FTT_CUDA(cudaMemsetAsync(SW.get(), 0, SW.bytes(), s));
     expand_cols_kernel<<<grid_for(dp.cols.nz * rr), 256, 0, s>>>(
@@ -373,8 +385,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
         sv.sigma.get(), rr, g.mid_cols, SW.get());
     FTT_LAUNCH();
     if (p < d) {
-      // G_p := U_X ; G_{p+1} := G_{p+1} x_1 (Sigma V^T)  (right quasi-permutation core)
-      G[p] = std::move(UX);
+      // G_p := U_X (held as U_C) ; G_{p+1} := G_{p+1} x_1 (Sigma V^T)  (right quasi-permutation core)
       r[p] = rr;
       const int k1 = p + 1;
       DBuf<double> Gn((size_t)rr * n[k1 - 1] * r[k1], s);
@@ -441,10 +452,19 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
       DBuf<double> US((size_t)M * q, s);
       scale_cols_kernel<<<grid_for(M * q), 256, 0, s>>>(sv.U.get(), M, q, sv.sigma.get(), US.get());
       FTT_LAUNCH();
-      const int64_t Mp = r[k - 2] * n[k - 2];
-      DBuf<double> Gp((size_t)Mp * q, s);
-      gemm_f64(Mp, q, M, 1.0, G[k - 1].get(), M, 1, US.get(), q, 1, 0.0, Gp.get(), q, 1, s);
-      G[k - 1] = std::move(Gp);
+      if (k - 1 == p && UC.get()) {
+        // G_p = Q_S UC:  G_p R^T = Q_S (UC R^T), a beta_r-row GEMM, then one expansion
+        const int64_t br = dp.rows.beta;
+        DBuf<double> UC2((size_t)br * q, s);
+        gemm_f64(br, q, M, 1.0, UC.get(), M, 1, US.get(), q, 1, 0.0, UC2.get(), q, 1, s);
+        UC.reset();
+        G[p] = expand_Q_S(UC2.get(), q);
+      } else {
+        const int64_t Mp = r[k - 2] * n[k - 2];
+        DBuf<double> Gp((size_t)Mp * q, s);
+        gemm_f64(Mp, q, M, 1.0, G[k - 1].get(), M, 1, US.get(), q, 1, 0.0, Gp.get(), q, 1, s);
+        G[k - 1] = std::move(Gp);
+      }
       r[k - 1] = q;
     }
     start = p;

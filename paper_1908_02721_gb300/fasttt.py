@@ -55,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("ms_group", ctypes.c_double), ("ms_depar", ctypes.c_double), ("ms_round", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("flop_gemm", ctypes.c_double),
                 ("ms_jacobi", ctypes.c_double), ("flop_jacobi", ctypes.c_double), ("ms_sort", ctypes.c_double),
-                ("bytes_sort", ctypes.c_double)]
+                ("bytes_sort", ctypes.c_double), ("ms_jacobi32", ctypes.c_double),
+                ("flop_jacobi32", ctypes.c_double)]
 
     def to_dict(self):
         d = self.d
@@ -67,7 +68,8 @@ class Stats(ctypes.Structure):
                 "deltas": list(self.deltas[:d + 1]), "ms_ingest": self.ms_ingest, "ms_group": self.ms_group,
                 "ms_depar": self.ms_depar, "ms_round": self.ms_round, "ms_total": self.ms_total,
                 "ms_gemm": self.ms_gemm, "flop_gemm": self.flop_gemm, "ms_jacobi": self.ms_jacobi,
-                "flop_jacobi": self.flop_jacobi, "ms_sort": self.ms_sort, "bytes_sort": self.bytes_sort}
+                "flop_jacobi": self.flop_jacobi, "ms_sort": self.ms_sort, "bytes_sort": self.bytes_sort,
+                "ms_jacobi32": self.ms_jacobi32, "flop_jacobi32": self.flop_jacobi32}
 
 
 _P = ctypes.c_void_p
