@@ -96,8 +96,10 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _workload(rank):
+def _workload(rank, name="uniform5"):
     from paper_1908_02721_gb300 import workloads as W
+    if name == "uniform5-n30":   # small case of the same recipe (profiling captures)
+        return W.uniform5(seed=2 + 1000 * rank, nnz=int(round(100_000 * (SAMPLE_N / 50) ** 5)), n=SAMPLE_N)
     return W.uniform5(seed=2 + 1000 * rank)
 
 
@@ -155,7 +157,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = _workload(rank)
+    w = _workload(rank, args.workload)
     idx = torch.from_numpy(w.idx).to(dev)
     vals = torch.from_numpy(w.vals).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -221,7 +223,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "5-way 50^5, 1e5 distinct uniform positions, N(0,1), eps=1e-8, FP64 FastTT",
+            "config": {"workload": ("5-way 50^5, 1e5 distinct uniform positions, N(0,1), eps=1e-8, FP64 FastTT"
+                                    if args.workload == "uniform5" else f"profiling case {args.workload}"),
                        "nnz": w.nnz, "dims": w.dims, "eps": w.eps, "p": st["p"], "ranks": st["ranks"],
                        "rt": st["rt"], "beta": [st["beta_r"], st["beta_c"]],
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
@@ -278,6 +281,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    ap.add_argument("--workload", default="uniform5", choices=["uniform5", "uniform5-n30"],
+                    help="uniform5-n30: the same recipe at 30^5, for profiler captures only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -372,11 +372,11 @@ __global__ void gather_rows_kernel(const double* src, int64_t ld, int64_t cols, 
 // same rotations.  Returns the number of sweeps; -1 if the bound was hit.
 template <typename T>
 int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ldv, int64_t max_sweeps,
-               cudaStream_t s) {
+               cudaStream_t s, double cos_tol = 0.0) {
   if (n < 2) return 0;
   const int n2 = n + (n & 1);
   const bool f64 = sizeof(T) == 8;
-  const T tol = (T)(sqrt((double)m) * (f64 ? 0x1p-52 : 0x1p-23));
+  const T tol = (T)std::max(cos_tol, sqrt((double)m) * (f64 ? 0x1p-52 : 0x1p-23));
   T small2;
   {
     DBuf<T> norms(n, s);
@@ -527,7 +527,8 @@ int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& 
     FTT_LAUNCH();
     identity_f32_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), n);
     FTT_LAUNCH();
-    sweeps = jacobi<float>(G32.get(), n, n, n, V32.get(), n, n, max_sweeps, s);  // a starting point only
+    // a starting point only: columns cosines below 1e-4 are left to the refinement
+    sweeps = jacobi<float>(G32.get(), n, n, n, V32.get(), n, n, max_sweeps, s, 1e-4);
     to_f64_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), nn, V);
     FTT_LAUNCH();
   }
@@ -535,7 +536,8 @@ int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& 
   const double gF = sqrt(g2);
   DBuf<double> R(nn, s), W(nn, s), S(nn, s), lam(n, s);
   lam_out.assign(n, 0.0);
-  for (int it = 0; it < 6; ++it) {
+  double prev = INFINITY;
+  for (int it = 0; it < 8; ++it) {
     // X^T is V's memory (row-major, row j = eigenvector j)
     gemm_f64(n, n, n, 1.0, V, n, 1, V, 1, n, 0.0, R.get(), n, 1, s, true);           // X^T X
     i_minus_kernel<<<grid_for(nn), 256, 0, s>>>(R.get(), n);
@@ -549,8 +551,13 @@ int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& 
     FTT_CUDA(cudaMemcpyAsync(lam_out.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
     if (!std::isfinite(offS) || !std::isfinite(rF)) fail(FASTTT_ENUMERIC, "non-finite eigen refinement");
-    const double tiny = 4.0 * (double)n * 0x1p-53;
-    if (rF <= tiny && offS <= tiny * gF) break;   // X orthonormal and S diagonal to rounding
+    // converged when X is orthonormal and S diagonal at the rounding level of the
+    // n-term FP64 products, or when the (quadratically converging) error stopped
+    // shrinking, i.e. reached that level
+    const double tiny = 64.0 * (double)n * 0x1p-53;
+    const double err = rF + offS / gF;
+    if ((rF <= tiny && offS <= tiny * gF) || err > 0.25 * prev) break;
+    prev = err;
     const double delta = 2.0 * (offS + gF * rF);
     oa_correction_kernel<<<grid_for(nn), 256, 0, s>>>(S.get(), R.get(), lam.get(), delta, n, W.get());  // W <- E
     FTT_LAUNCH();

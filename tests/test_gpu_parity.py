@@ -295,3 +295,43 @@ def test_eval_float32_and_bad_index(F):
     with pytest.raises(F.FastTTError) as e:
         F.tt_eval_at(tc, np.array([[0], [1], [4]], dtype=np.int32))
     assert e.value.code == F.EINVAL
+
+
+def test_banded_qtt_m10(F):
+    """2^10 x 2^10 band + off-band matrix as a 10-way QTT tensor (eps = 1e-6): grouping
+    bit-exact (Alg. 9 picks p), ranks equal, products within 1e-12."""
+    w = W.banded_qtt(10)
+    res = _full_check(F, w, w.eps)
+    assert max(res.ranks) > 900    # the random off-band entries keep the ranks high
+
+
+def test_uniform5_full_size_properties(F):
+    """The bench workload (50^5, 1e5 nonzeros, eps = 1e-8) at full size: ranks, r~, beta and R
+    against the oracle's grouping, and B reproduces A at sampled nonzeros and zeros."""
+    w = W.uniform5()
+    tt = F.fasttt_decompose(w.idx, w.vals, w.dims, w.eps)
+    ex = O.exact_tt(w.idx.astype(np.int64), w.vals, w.dims, tt.stats["p"])
+    Rs = [O.fiber_ids(w.idx.astype(np.int64), q)[0] for q in range(1, w.d + 1)]
+    p, _ = O.select_p(w.dims, Rs)
+    assert tt.stats["p"] == p and tt.stats["Rs"] == Rs and tt.stats["rt"] == ex.rt
+    dp = O.value_depar(ex.mid_rows, ex.mid_cols, ex.mid_vals)
+    assert (tt.stats["beta_r"], tt.stats["beta_c"]) == (dp.beta_r, dp.beta_c)
+    # every bond is well conditioned and eps = 1e-8: the TT keeps the full unfolding ranks
+    assert tt.ranks == [1, 50, 2500, 2500, 50, 1]
+    cores = tt.cores()
+    rng = np.random.Generator(np.random.Philox(key=701))
+    pick = rng.choice(w.nnz, 20000, replace=False)
+    a = _np(F.tt_eval_at(cores, w.idx[:, pick]))
+    nA = math.sqrt(tt.stats["norm2"])
+    assert np.linalg.norm(a - w.vals[pick]) <= 1e-8 * nA
+    zeros = np.stack([rng.integers(0, 50, 20000) for _ in range(5)]).astype(np.int32)
+    lin = lambda I: sum(I[k].astype(np.int64) * 50 ** (4 - k) for k in range(5))
+    zeros = zeros[:, ~np.isin(lin(zeros), lin(w.idx))]
+    z = _np(F.tt_eval_at(cores, zeros))
+    assert np.linalg.norm(z) <= 1e-8 * nA
+    # cores 2..d are right-orthonormal after Alg. 6 (second sweep / QR sweep)
+    for k in range(2, 6):
+        G = cores[k - 1].reshape(cores[k - 1].shape[0], -1)
+        I = G @ G.T
+        assert torch.allclose(I, torch.eye(I.shape[0], dtype=I.dtype, device=I.device), atol=1e-12)
+    tt.free()
