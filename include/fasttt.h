@@ -50,6 +50,13 @@ extern "C" {
 
 /* fasttt_opts.precision */
 #define FASTTT_PREC_FP64 0   /* every floating-point step in IEEE FP64 */
+#define FASTTT_PREC_MIXED 1  /* the large contractions (Gram matrices, projections, merges)
+                              * as split-TF32 tensor-core GEMMs with FP32 accumulation and
+                              * tensor-core re-orthonormalisation of the kept factors; Gram
+                              * eigenvectors by FP32 Jacobi; eigenvalues (Rayleigh quotients),
+                              * rank rule, norms and small (direct-route) SVDs in FP64.
+                              * FP32-level accuracy (~1e-6 relative): rank decisions match
+                              * FP64 where the discarded tail is above that level. */
 
 /* fasttt_opts.rounding */
 #define FASTTT_STATIC 0      /* delta_k of eq. (11), Alg. 6 */
@@ -61,7 +68,7 @@ extern "C" {
 
 typedef struct fasttt_opts {
   int p;              /* split point 1..d; 0 = choose by Alg. 9 (flop model, eq. (13)) */
-  int precision;      /* FASTTT_PREC_FP64 */
+  int precision;      /* FASTTT_PREC_FP64 or FASTTT_PREC_MIXED */
   int rounding;       /* FASTTT_STATIC or FASTTT_DYNAMIC */
   int depar_values;   /* 1: value Depar (Alg. 3, exact parallelism) of the middle unfolding; 0: off */
   int stage;          /* FASTTT_STAGE_FULL or FASTTT_STAGE_EXACT */
@@ -94,7 +101,8 @@ typedef struct fasttt_stats {
    * (2MNK flops), Jacobi sweeps (dot products + applied rotations, flops) and
    * radix-sort passes (key/value bytes moved) */
   double ms_gemm, flop_gemm, ms_jacobi, flop_jacobi, ms_sort, bytes_sort;
-  double ms_jacobi32, flop_jacobi32; /* the FP32 Jacobi sweeps that precondition large eigenproblems */
+  double ms_jacobi32, flop_jacobi32; /* FP32 Jacobi sweeps (large eigenproblems) */
+  double ms_gemm_tc, flop_gemm_tc;   /* split-TF32 tensor-core GEMMs (mixed precision) */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */

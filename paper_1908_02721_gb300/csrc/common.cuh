@@ -45,7 +45,7 @@ int64_t launch_count();
 
 // Per-call device timing of the heavy kernel classes, by CUDA events on the
 // launching stream (read once at the end of a call).
-enum KernelClass { KC_GEMM = 0, KC_JACOBI = 1, KC_SORT = 2, KC_JACOBI32 = 3, KC_COUNT = 4 };
+enum KernelClass { KC_GEMM = 0, KC_JACOBI = 1, KC_SORT = 2, KC_JACOBI32 = 3, KC_GEMM_TC = 4, KC_COUNT = 5 };
 struct KClock {
   cudaEvent_t a = nullptr, b = nullptr;
   int cls = 0;

@@ -33,6 +33,7 @@ namespace {
 constexpr int kTile = 64;
 constexpr int kTileK = 16;
 constexpr int kDirectMax = 512;
+constexpr int kOrthoLeft = 1, kOrthoRight = 2;
 
 __global__ void __launch_bounds__(256)
     gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A, int64_t sai,
@@ -350,6 +351,11 @@ __global__ void mirror_upper_kernel(double* C, int64_t n) {
     if (i > j) C[e] = C[j * n + i];
   }
 }
+// out (M x r) = U (M x r) with column c scaled by scale[c]
+__global__ void scale_cols_kernel2(const double* U, int64_t M, int64_t r, const double* scale, double* out) {
+  GRID_STRIDE(e, M * r) out[e] = U[e] * scale[e % r];
+}
+
 // out (rows x r, row-major): out[i, c] = src[perm[c] * ld + i] * scale[c]
 __global__ void gather_cols_kernel(const double* src, int64_t ld, int64_t rows, const int32_t* perm,
                                    const double* scale, int64_t r, double* out) {
@@ -472,6 +478,18 @@ __global__ void __launch_bounds__(256) sumsq_offdiag_kernel(const double* M, con
   }
 }
 
+// y = M v - d .* v (d may be null); one warp per row of the n x n row-major M
+__global__ void matvec_kernel(const double* M, const double* d, const double* v, int64_t n, double* y) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32) acc = fma(M[row * n + j], v[j], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = d ? acc - d[row] * v[row] : acc;
+}
+
 // R <- I - R (R holds X^T X on entry)
 __global__ void i_minus_kernel(double* R, int64_t n) {
   GRID_STRIDE(e, n * n) R[e] = ((e / n) == (e % n) ? 1.0 : 0.0) - R[e];
@@ -491,6 +509,30 @@ __global__ void oa_correction_kernel(const double* S, const double* R, const dou
     const double d = lam[j] - lam[i];
     E[e] = (i != j && fabs(d) > delta) ? (S[e] + lam[j] * R[e]) / d : 0.5 * R[e];
   }
+}
+
+// ||M - diag(d)||_2 of a symmetric n x n matrix by 12 steps of the power method
+// from a fixed start (an estimate from below; callers add a safety factor)
+double norm2_sym(const double* M, const double* d, int64_t n, cudaStream_t s) {
+  std::vector<double> h(n);
+  for (int64_t i = 0; i < n; ++i) h[i] = 1.0 + 0.5 * sin(0.7 * (double)i + 0.3);
+  DBuf<double> v(n, s), y(n, s);
+  FTT_CUDA(cudaMemcpyAsync(v.get(), h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  double est = 0.0;
+  for (int it = 0; it < 12; ++it) {
+    matvec_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(M, d, v.get(), n, y.get());
+    FTT_LAUNCH();
+    FTT_CUDA(cudaMemcpyAsync(h.data(), y.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    double nrm = 0.0;
+    for (double x : h) nrm += x * x;
+    nrm = sqrt(nrm);
+    if (!(nrm > 0.0)) return 0.0;
+    est = nrm;   // ||M v|| with ||v|| = 1 after the first step
+    for (auto& x : h) x /= nrm;
+    FTT_CUDA(cudaMemcpyAsync(v.get(), h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  }
+  return est;
 }
 
 double sumsq(const double* M, const double* diag, int64_t n, cudaStream_t s) {
@@ -527,8 +569,7 @@ int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& 
     FTT_LAUNCH();
     identity_f32_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), n);
     FTT_LAUNCH();
-    // a starting point only: columns cosines below 1e-4 are left to the refinement
-    sweeps = jacobi<float>(G32.get(), n, n, n, V32.get(), n, n, max_sweeps, s, 1e-4);
+    sweeps = jacobi<float>(G32.get(), n, n, n, V32.get(), n, n, max_sweeps, s);  // a starting point only
     to_f64_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), nn, V);
     FTT_LAUNCH();
   }
@@ -551,20 +592,112 @@ int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& 
     FTT_CUDA(cudaMemcpyAsync(lam_out.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
     if (!std::isfinite(offS) || !std::isfinite(rF)) fail(FASTTT_ENUMERIC, "non-finite eigen refinement");
-    // converged when X is orthonormal and S diagonal at the rounding level of the
-    // n-term FP64 products, or when the (quadratically converging) error stopped
-    // shrinking, i.e. reached that level
+    // Continue while the (quadratically converging) error keeps shrinking; stop at
+    // the rounding level of the n-term FP64 products or when it stalls (eigenvalue
+    // clusters closer than the refinement can separate: the polish resolves them).
     const double tiny = 64.0 * (double)n * 0x1p-53;
     const double err = rF + offS / gF;
     if ((rF <= tiny && offS <= tiny * gF) || err > 0.25 * prev) break;
     prev = err;
-    const double delta = 2.0 * (offS + gF * rF);
+    // delta of the refinement with 2-norms (power-method estimates with a safety
+    // factor of 2; Frobenius norms would overstate them by up to sqrt(n))
+    const double s2 = std::min(offS, 2.0 * norm2_sym(S.get(), lam.get(), n, s));
+    const double r2 = std::min(rF, 2.0 * norm2_sym(R.get(), nullptr, n, s));
+    double lmax = 0.0;
+    for (double x : lam_out) lmax = std::max(lmax, fabs(x));
+    const double delta = 2.0 * (s2 + lmax * r2);
     oa_correction_kernel<<<grid_for(nn), 256, 0, s>>>(S.get(), R.get(), lam.get(), delta, n, W.get());  // W <- E
     FTT_LAUNCH();
     // X <- X + X E, in X^T layout: X^T <- X^T + E^T X^T
     FTT_CUDA(cudaMemcpyAsync(S.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
     gemm_f64(n, n, n, 1.0, W.get(), 1, n, S.get(), n, 1, 1.0, V, n, 1, s);
   }
+  // Orthonormalise X to FP64 rounding (Newton-Schulz: X <- 1.5 X - 0.5 X (X^T X),
+  // quadratic while ||I - X^T X|| < 1), whatever the refinement left.
+  for (int it = 0; it < 3; ++it) {
+    gemm_f64(n, n, n, 1.0, V, n, 1, V, 1, n, 0.0, R.get(), n, 1, s, true);            // S = X^T X
+    i_minus_kernel<<<grid_for(nn), 256, 0, s>>>(R.get(), n);
+    FTT_LAUNCH();
+    const double rF = sqrt(sumsq(R.get(), nullptr, n, s));
+    if (!(rF < 0.5)) fail(FASTTT_ENUMERIC, "eigenvector basis lost orthogonality");
+    if (rF <= 16.0 * (double)n * 0x1p-53) break;
+    // in X^T layout: X^T <- X^T + 0.5 (I - X^T X) X^T  (equivalent to the Newton-Schulz step)
+    FTT_CUDA(cudaMemcpyAsync(S.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    gemm_f64(n, n, n, 0.5, R.get(), n, 1, S.get(), n, 1, 1.0, V, n, 1, s);
+  }
+  // Polish: FP64 one-sided Jacobi on A = G X with the rotations accumulated into X
+  // (column-major); converged columns have norms lambda_j.  Rotates little when the
+  // refinement converged; resolves eigenvalue clusters it left mixed.
+  gemm_f64(n, n, n, 1.0, V, n, 1, G, n, 1, 0.0, W.get(), n, 1, s);   // row j of A^T = (G x_j)^T
+  jacobi_f64(W.get(), n, n, n, V, n, n, max_sweeps, s);
+  DBuf<double> norms(n, s);
+  col_norms_kernel<double><<<n, 256, 0, s>>>(W.get(), n, n, n, norms.get());
+  FTT_LAUNCH();
+  FTT_CUDA(cudaMemcpyAsync(lam_out.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaStreamSynchronize(s));
+  return sweeps;
+}
+
+// Orthonormalise the columns of the row-major rows x r matrix U on the tensor
+// cores: U <- U + 0.5 U (I - U^T U), twice (quadratic while ||I - U^T U|| < 1).
+void orthonormalise_cols_tc(double* U, int64_t rows, int64_t r, cudaStream_t s) {
+  DBuf<double> S((size_t)r * r, s), U0((size_t)rows * r, s);
+  for (int it = 0; it < 2; ++it) {
+    gemm_tf32x3(r, r, rows, 1.0, U, 1, r, U, r, 1, 0.0, S.get(), r, 1, s, true);   // U^T U
+    i_minus_kernel<<<grid_for(r * r), 256, 0, s>>>(S.get(), r);
+    FTT_LAUNCH();
+    FTT_CUDA(cudaMemcpyAsync(U0.get(), U, sizeof(double) * rows * r, cudaMemcpyDeviceToDevice, s));
+    gemm_tf32x3(rows, r, r, 0.5, U0.get(), r, 1, S.get(), r, 1, 1.0, U, r, 1, s);
+  }
+}
+
+// out[i] = (row i of X) . (row i of Y), den[i] = |row i of X|^2 (n x n row-major, FP64 sums)
+__global__ void row_dots_kernel(const double* X, const double* Y, int64_t n, double* num, double* den) {
+  const int64_t i = blockIdx.x;
+  double a = 0.0, b = 0.0, z = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double x = X[i * n + j];
+    a = fma(x, Y[i * n + j], a);
+    b = fma(x, x, b);
+  }
+  block_sum3<double>(a, b, z);
+  if (threadIdx.x == 0) { num[i] = a; den[i] = b; }
+}
+
+// Mixed-precision eigendecomposition of the symmetric PSD Gram G (n x n): FP32
+// one-sided Jacobi to FP32 convergence gives V; the eigenvalues are the Rayleigh
+// quotients v^T G v / v^T v with G V on the tensor cores and the dot products in
+// FP64.  FP32-level accuracy; the caller re-orthonormalises what it keeps.
+int64_t sym_eig_mixed32(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps,
+                        cudaStream_t s) {
+  const int64_t nn = (int64_t)n * n;
+  int64_t sweeps;
+  {
+    DBuf<float> G32(nn, s), V32(nn, s);
+    to_f32_kernel<<<grid_for(nn), 256, 0, s>>>(G, nn, G32.get());
+    FTT_LAUNCH();
+    identity_f32_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), n);
+    FTT_LAUNCH();
+    sweeps = jacobi<float>(G32.get(), n, n, n, V32.get(), n, n, max_sweeps, s);
+    if (sweeps < 0) fail(FASTTT_ETIMEOUT, "FP32 Jacobi did not converge within the sweep bound");
+    to_f64_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), nn, V);
+    FTT_LAUNCH();
+  }
+  // FP32 rotations accumulated over all sweeps leave V orthonormal only to ~1e-4:
+  // restore it (columns of V = rows of its row-major memory)
+  DBuf<double> W(nn, s), num(n, s), den(n, s);
+  transpose_f64(V, n, n, W.get(), s);
+  orthonormalise_cols_tc(W.get(), n, n, s);
+  transpose_f64(W.get(), n, n, V, s);
+  gemm_tf32x3(n, n, n, 1.0, V, n, 1, G, n, 1, 0.0, W.get(), n, 1, s);   // row i = (G v_i)^T
+  row_dots_kernel<<<n, 256, 0, s>>>(V, W.get(), n, num.get(), den.get());
+  FTT_LAUNCH();
+  std::vector<double> hn(n), hd(n);
+  FTT_CUDA(cudaMemcpyAsync(hn.data(), num.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaMemcpyAsync(hd.data(), den.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaStreamSynchronize(s));
+  lam_out.resize(n);
+  for (int i = 0; i < n; ++i) lam_out[i] = hd[i] > 0.0 ? hn[i] / hd[i] : 0.0;
   return sweeps;
 }
 
@@ -600,13 +733,14 @@ void transpose_f64(const double* src, int64_t rows, int64_t cols, double* dst, c
 
 void svd_truncated(const double* Z, int64_t M, int64_t N,
                    const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
-                   SvdOut& out, cudaStream_t s) {
+                   SvdOut& out, cudaStream_t s, bool mixed, int ortho) {
   const bool tall = (M >= N);
   const int64_t sm = tall ? N : M;   // number of singular values
   const int64_t lg = tall ? M : N;
   if (sm > INT32_MAX / 2) fail(FASTTT_ERANK, "SVD too large");
   const int n = (int)sm;
-  const bool direct = (sm <= kDirectMax);
+  // direct (accurate) route while a Jacobi sweep stays below ~4e10 flops
+  const bool direct = (sm <= kDirectMax) || (9.0 * (double)lg * (double)sm * (double)sm <= 4.0e10);
   DBuf<double> A;      // column-major lg x n (direct) or n x n (Gram)
   int64_t m_len, lda;
   if (direct) {
@@ -618,9 +752,9 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
   } else {
     A = DBuf<double>((size_t)n * n, s);
     if (tall)  // G = Z^T Z
-      gemm_f64(N, N, M, 1.0, Z, 1, N, Z, N, 1, 0.0, A.get(), N, 1, s, true);
+      gemm(mixed, N, N, M, 1.0, Z, 1, N, Z, N, 1, 0.0, A.get(), N, 1, s, true);
     else       // G = Z Z^T
-      gemm_f64(M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, A.get(), M, 1, s, true);
+      gemm(mixed, M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, A.get(), M, 1, s, true);
     m_len = n;
     lda = n;
   }
@@ -636,7 +770,8 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
     FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
   } else {
-    out.sweeps = sym_eig_refined(A.get(), n, V.get(), h, max_sweeps, s);
+    out.sweeps = mixed ? sym_eig_mixed32(A.get(), n, V.get(), h, max_sweeps, s)
+                       : sym_eig_refined(A.get(), n, V.get(), h, max_sweeps, s);
     for (auto& x : h) x = sqrt(std::max(x, 0.0));  // eigenvalues of the Gram -> singular values
   }
   for (double x : h)
@@ -676,14 +811,35 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
     FTT_LAUNCH();
     gather_rows_kernel<<<grid_for(r * N), 256, 0, s>>>(V.get(), n, N, dperm.get(), nullptr, r, out.Vt.get());
     FTT_LAUNCH();
-    gemm_f64(M, r, N, 1.0, Z, N, 1, Vs.get(), r, 1, 0.0, out.U.get(), r, 1, s);
+    gemm(mixed, M, r, N, 1.0, Z, N, 1, Vs.get(), r, 1, 0.0, out.U.get(), r, 1, s);
+    if (mixed && ortho == kOrthoLeft) {
+      // U = Z V Sigma^-1 carries the FP32-level product error times sigma_1 / sigma_r:
+      // make U orthonormal again and take Vt = Sigma^-1 U^T Z (U Sigma Vt = U U^T Z)
+      orthonormalise_cols_tc(out.U.get(), M, r, s);
+      DBuf<double> Us((size_t)M * r, s);
+      scale_cols_kernel2<<<grid_for(M * r), 256, 0, s>>>(out.U.get(), M, r, dinv.get(), Us.get());
+      FTT_LAUNCH();
+      gemm(mixed, r, N, M, 1.0, Us.get(), 1, r, Z, N, 1, 0.0, out.Vt.get(), N, 1, s);
+    }
   } else {            // V: left vectors; Vt = Sigma^-1 U_r^T Z
     gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(V.get(), n, M, dperm.get(), nullptr, r, out.U.get());
     FTT_LAUNCH();
     DBuf<double> Us((size_t)M * r, s);
     gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(V.get(), n, M, dperm.get(), dinv.get(), r, Us.get());
     FTT_LAUNCH();
-    gemm_f64(r, N, M, 1.0, Us.get(), 1, r, Z, N, 1, 0.0, out.Vt.get(), N, 1, s);
+    gemm(mixed, r, N, M, 1.0, Us.get(), 1, r, Z, N, 1, 0.0, out.Vt.get(), N, 1, s);
+    if (mixed && ortho == kOrthoRight) {
+      // Vt = Sigma^-1 U^T Z: make its rows orthonormal again (columns of Vt^T) and take
+      // U = Z Vt^T Sigma^-1, so that U Sigma Vt = Z Vt^T Vt
+      DBuf<double> Vc((size_t)N * r, s);
+      transpose_f64(out.Vt.get(), r, N, Vc.get(), s);
+      orthonormalise_cols_tc(Vc.get(), N, r, s);
+      transpose_f64(Vc.get(), N, r, out.Vt.get(), s);
+      DBuf<double> ZV((size_t)M * r, s);
+      gemm(mixed, M, r, N, 1.0, Z, N, 1, Vc.get(), r, 1, 0.0, ZV.get(), r, 1, s);
+      scale_cols_kernel2<<<grid_for(M * r), 256, 0, s>>>(ZV.get(), M, r, dinv.get(), out.U.get());
+      FTT_LAUNCH();
+    }
   }
 }
 

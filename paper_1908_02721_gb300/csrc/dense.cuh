@@ -16,6 +16,20 @@ void gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, in
               const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
               cudaStream_t s, bool sym = false);
 
+// The same product as gemm_f64 on the tensor cores: split-TF32 operands (3
+// products), FP32 accumulation, FP64 in and out.  FP32-level accuracy.
+void gemm_tf32x3(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
+                 const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
+                 cudaStream_t s, bool sym = false);
+
+// gemm_f64 or, with mixed = true, gemm_tf32x3.
+inline void gemm(bool mixed, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai,
+                 int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci,
+                 int64_t scj, cudaStream_t s, bool sym = false) {
+  if (mixed) gemm_tf32x3(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  else gemm_f64(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+}
+
 // dst (cols x rows, row-major) = transpose of src (rows x cols, row-major)
 void transpose_f64(const double* src, int64_t rows, int64_t cols, double* dst, cudaStream_t s);
 
@@ -28,7 +42,14 @@ struct SvdOut {
   DBuf<double> U, sigma, Vt;
   int64_t sweeps = 0;
 };
+// mixed = true: the Gram and the projections run on the tensor cores
+// (gemm_tf32x3, FP32-level accuracy), the n x n eigenproblem of large Grams in
+// FP32 Jacobi with FP64 Rayleigh quotients; the direct route stays FP64.
+// ortho = 1 (left): U must come out orthonormal; 2 (right): the rows of Vt must.
+// In mixed precision the factor that the tall-side product amplifies by
+// sigma_1 / sigma_r is re-orthonormalised on the tensor cores and its partner
+// recomputed (the re-orthogonalisation that keeps FP32-level products usable).
 void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<int64_t(const std::vector<double>&)>& choose_rank,
-                   int64_t max_sweeps, SvdOut& out, cudaStream_t s);
+                   int64_t max_sweeps, SvdOut& out, cudaStream_t s, bool mixed = false, int ortho = 0);
 
 }  // namespace fasttt

@@ -261,6 +261,8 @@ void finish_stats(fasttt_stats& st, int64_t launches0) {
   st.bytes_sort = work[KC_SORT];
   st.ms_jacobi32 = ms[KC_JACOBI32];
   st.flop_jacobi32 = work[KC_JACOBI32];
+  st.ms_gemm_tc = ms[KC_GEMM_TC];
+  st.flop_gemm_tc = work[KC_GEMM_TC];
   kclock_reset();
   st.launches = launch_count() - launches0;
 }
@@ -275,7 +277,8 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
          double eps, const fasttt_opts& o, cudaStream_t s, Handle& H) {
   if (!(eps >= 0.0) || !std::isfinite(eps)) fail(FASTTT_EINVAL, "eps must be finite and >= 0");
   if (o.rounding != FASTTT_STATIC && o.rounding != FASTTT_DYNAMIC) fail(FASTTT_EINVAL, "bad rounding mode");
-  if (o.precision != FASTTT_PREC_FP64) fail(FASTTT_EINVAL, "unsupported precision");
+  if (o.precision != FASTTT_PREC_FP64 && o.precision != FASTTT_PREC_MIXED) fail(FASTTT_EINVAL, "unsupported precision");
+  const bool mixed = (o.precision == FASTTT_PREC_MIXED);
   if (o.stage != FASTTT_STAGE_FULL && o.stage != FASTTT_STAGE_EXACT) fail(FASTTT_EINVAL, "bad stage");
   const int64_t max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
   fasttt_stats& st = H.st;
@@ -366,7 +369,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
     SvdOut sv;
     svd_truncated(C.get(), br, bc, [&](const std::vector<double>& sg) {
       return rank_rule(sg, dl, eps0, n, bond, o.max_rank);
-    }, max_sweeps, sv, s);
+    }, max_sweeps, sv, s, mixed, 1);  // U_C becomes G_p (p < d) or G_d^T (p = d)
     C.reset();
     const double e2 = record(bond, sv, dl);
     const int64_t rr = sv.r;
@@ -422,7 +425,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
       SvdOut sv;
       svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) {
         return rank_rule(sg, dl, eps0, n, k, o.max_rank);
-      }, max_sweeps, sv, s);
+      }, max_sweeps, sv, s, mixed, 1);
       const double e2 = record(k, sv, dl);
       const int64_t rr = sv.r;
       G[k] = std::move(sv.U);
@@ -445,7 +448,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
       const int64_t M = r[k - 1], N = n[k - 1] * r[k];
       SvdOut sv;
       svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) { return (int64_t)sg.size(); },
-                    max_sweeps, sv, s);
+                    max_sweeps, sv, s, mixed, 2);
       st.jacobi_sweeps += sv.sweeps;
       const int64_t q = sv.r;
       G[k] = std::move(sv.Vt);
@@ -456,13 +459,13 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
         // G_p = Q_S UC:  G_p R^T = Q_S (UC R^T), a beta_r-row GEMM, then one expansion
         const int64_t br = dp.rows.beta;
         DBuf<double> UC2((size_t)br * q, s);
-        gemm_f64(br, q, M, 1.0, UC.get(), M, 1, US.get(), q, 1, 0.0, UC2.get(), q, 1, s);
+        gemm(mixed, br, q, M, 1.0, UC.get(), M, 1, US.get(), q, 1, 0.0, UC2.get(), q, 1, s);
         UC.reset();
         G[p] = expand_Q_S(UC2.get(), q);
       } else {
         const int64_t Mp = r[k - 2] * n[k - 2];
         DBuf<double> Gp((size_t)Mp * q, s);
-        gemm_f64(Mp, q, M, 1.0, G[k - 1].get(), M, 1, US.get(), q, 1, 0.0, Gp.get(), q, 1, s);
+        gemm(mixed, Mp, q, M, 1.0, G[k - 1].get(), M, 1, US.get(), q, 1, 0.0, Gp.get(), q, 1, s);
         G[k - 1] = std::move(Gp);
       }
       r[k - 1] = q;
@@ -479,7 +482,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
     SvdOut sv;
     svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) {
       return rank_rule(sg, dl, eps0, n, k - 1, o.max_rank);
-    }, max_sweeps, sv, s);
+    }, max_sweeps, sv, s, mixed, 2);
     const double e2 = record(k - 1, sv, dl);
     const int64_t rr = sv.r;
     G[k] = std::move(sv.Vt);

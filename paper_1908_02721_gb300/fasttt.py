@@ -23,6 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 MAX_D = 64
 OK, EINVAL, EDUP, ENOMEM, ETIMEOUT, ENUMERIC, ERANK, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
 F64, F32 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
 STATIC, DYNAMIC = 0, 1
 STAGE_FULL, STAGE_EXACT = 0, 1
 ARR = {name: i for i, name in enumerate([
@@ -56,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("flop_gemm", ctypes.c_double),
                 ("ms_jacobi", ctypes.c_double), ("flop_jacobi", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("bytes_sort", ctypes.c_double), ("ms_jacobi32", ctypes.c_double),
-                ("flop_jacobi32", ctypes.c_double)]
+                ("flop_jacobi32", ctypes.c_double), ("ms_gemm_tc", ctypes.c_double),
+                ("flop_gemm_tc", ctypes.c_double)]
 
     def to_dict(self):
         d = self.d
@@ -69,7 +71,8 @@ class Stats(ctypes.Structure):
                 "ms_depar": self.ms_depar, "ms_round": self.ms_round, "ms_total": self.ms_total,
                 "ms_gemm": self.ms_gemm, "flop_gemm": self.flop_gemm, "ms_jacobi": self.ms_jacobi,
                 "flop_jacobi": self.flop_jacobi, "ms_sort": self.ms_sort, "bytes_sort": self.bytes_sort,
-                "ms_jacobi32": self.ms_jacobi32, "flop_jacobi32": self.flop_jacobi32}
+                "ms_jacobi32": self.ms_jacobi32, "flop_jacobi32": self.flop_jacobi32,
+                "ms_gemm_tc": self.ms_gemm_tc, "flop_gemm_tc": self.flop_gemm_tc}
 
 
 _P = ctypes.c_void_p
@@ -188,7 +191,7 @@ class TT:
 
 
 def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True, rounding="static",
-                     stage="full", keep_intermediates=False, max_sweeps=0, stream=None) -> TT:
+                     stage="full", keep_intermediates=False, max_sweeps=0, precision="fp64", stream=None) -> TT:
     """FastTT (Alg. 7) of the COO tensor (idx (d, nnz) int32, vals float64/float32)."""
     _require_cuda()
     idx = _dev(idx, torch.int32)
@@ -208,6 +211,7 @@ def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True
     o.stage = STAGE_EXACT if stage == "exact" else STAGE_FULL
     o.keep_intermediates = 1 if keep_intermediates else 0
     o.max_sweeps = int(max_sweeps)
+    o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
     out = ctypes.c_void_p(0)
     st = Stats()
     rc = _lib.fasttt_decompose(d, _i64arr(dims), int(idx.shape[1]), ctypes.c_void_p(idx.data_ptr()),
