@@ -197,6 +197,11 @@ def run_ours(args):
         ms = float(t.item())
     value = w.nnz * world / (ms / 1e3)
 
+    # accuracy of the timed configuration: relative error of B at a fixed sample of nonzeros
+    rel_err = _sampled_rel_err(F, idx, w, "fp64")
+    mixed_line = None if args.no_mixed else _mixed(args, F, idx, vals, w, flush, stream)
+    adjoint_line = None if args.no_adjoint else _adjoint(args, F, dev, stream)
+
     # e2e through the same C-ABI call from pinned host memory
     e2e_line = None
     if not args.no_e2e:
@@ -230,6 +235,9 @@ def run_ours(args):
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e_line,
+            "rel_err_sampled": rel_err,
+            "mixed": mixed_line,
+            "adjoint": adjoint_line,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm",
@@ -239,6 +247,89 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _sampled_rel_err(F, idx, w, precision, tt=None):
+    """||B - A|| / ||A|| over 20,000 fixed nonzeros (tt_eval_at on the decomposition)."""
+    import numpy as np
+    import torch
+    own = tt is None
+    if own:
+        tt = F.fasttt_decompose(idx, torch.from_numpy(w.vals).to(idx.device), w.dims, w.eps, precision=precision)
+    rng = np.random.Generator(np.random.Philox(key=99))
+    pick = rng.choice(w.nnz, min(20000, w.nnz), replace=False)
+    a = F.tt_eval_at(tt.cores(), torch.from_numpy(np.ascontiguousarray(w.idx[:, pick])).to(idx.device))
+    ref = w.vals[pick]
+    err = float(np.linalg.norm(a.cpu().numpy() - ref) / np.linalg.norm(ref))
+    if own:
+        tt.free()
+    return err
+
+
+def _mixed(args, F, idx, vals, w, flush, stream):
+    """The same workload in mixed precision (split-TF32 tensor-core contractions)."""
+    import torch
+    for _ in range(args.warmup):
+        F.fasttt_decompose(idx, vals, w.dims, w.eps, precision="mixed").free()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    st = None
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        tt = F.fasttt_decompose(idx, vals, w.dims, w.eps, precision="mixed")
+        ev[i][1].record(stream)
+        st = tt.stats
+        if i < args.steps - 1:
+            tt.free()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    err = _sampled_rel_err(F, idx, w, "mixed", tt)
+    tt.free()
+    tc = st["ms_gemm_tc"]
+    return {"value": w.nnz / (ms / 1e3), "unit": "nnz/s", "ms_per_step": ms, "rel_err_sampled": err,
+            "ranks": st["ranks"], "dtype": "tf32x3 tensor-core contractions + f32/f64",
+            "tensor_gemm": {"ms": tc, "tflops": st["flop_gemm_tc"] / (tc / 1e3) / 1e12 if tc else None},
+            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_tc", "ms_jacobi", "ms_jacobi32")}}
+
+
+def _adjoint(args, F, dev, stream):
+    """tt_eval_at + tt_eval_backward on every nonzero of the Zipf(1.2) 100^8 workload (1e7
+    entries) for FP32 TTs of rank 8 (the planted rank) and rank 64 (the rank cap)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1908_02721_gb300 import workloads as W
+    w = W.zipf_tt(nnz=10_000_000)
+    idx = torch.from_numpy(w.idx).to(dev)
+    m = w.nnz
+    out = {"workload": "Zipf(1.2) 8-way 100^8, 1e7 distinct entries, FP32 cores", "entries": m}
+    peaks, _ = _peaks()
+    hbm = peaks.get("hbm_gbs", 6686.8)
+    for r in (8, 64):
+        rng = np.random.Generator(np.random.Philox(key=400 + r))
+        ranks = [1] + [r] * 7 + [1]
+        cores = [torch.from_numpy((rng.standard_normal((ranks[k], 100, ranks[k + 1])) / math.sqrt(ranks[k]))
+                                  .astype(np.float32)).to(dev) for k in range(8)]
+        g = torch.from_numpy(rng.standard_normal(m).astype(np.float32)).to(dev)
+        grads = [torch.zeros_like(c) for c in cores]
+        for _ in range(2):
+            F.tt_eval_at(cores, idx)
+            F.tt_eval_backward(cores, idx, g, grads)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        F.tt_eval_at(cores, idx)
+        e[1].record(stream)
+        F.tt_eval_backward(cores, idx, g, grads)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        # algorithmic HBM bytes: indices (8 x 4 B) + upstream gradient (4 B) per entry, cores L2-resident
+        bytes_bwd = m * (8 * 4 + 4)
+        flops_bwd = m * (2 * 2 * sum(ranks[k] * ranks[k + 1] for k in range(8)) + 2 * sum(ranks[k] * ranks[k + 1] for k in range(8)))
+        out[f"rank{r}"] = {"eval_ms": fwd, "backward_ms": bwd, "backward_gbs": bytes_bwd / (bwd / 1e3) / 1e9,
+                           "backward_hbm_frac": bytes_bwd / (bwd / 1e3) / 1e9 / hbm,
+                           "backward_tflops": flops_bwd / (bwd / 1e3) / 1e12}
+    return out
 
 
 def _e2e(args, w, F, dev, barrier, world):
@@ -281,6 +372,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision pass")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--workload", default="uniform5", choices=["uniform5", "uniform5-n30"],
                     help="uniform5-n30: the same recipe at 30^5, for profiler captures only")
     args = ap.parse_args()
