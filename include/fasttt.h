@@ -93,6 +93,8 @@ typedef struct fasttt_stats {
   int64_t beta_r, beta_c;    /* row / column classes of the middle unfolding (value Depar) */
   int64_t jacobi_sweeps;     /* total Jacobi sweeps over all dense SVDs */
   int64_t launches;          /* CUDA kernels this call launched */
+  int64_t jacobi_block_sweeps; /* Jacobi sweeps run on the shared-memory block schedule */
+  int64_t coop_launch_error;   /* last error code of a refused cooperative launch (0: none) */
   double norm2;              /* ||A||_F^2 */
   double err2;               /* sum over truncations of the discarded sigma^2 (||E_k||_F^2) */
   double deltas[FASTTT_MAX_D + 1]; /* delta_k used at bond k (0 where unused) */

@@ -35,6 +35,11 @@ inline void cuda_check(cudaError_t e, const char* what, const char* file, int li
 // Kernel launches of this process (every launch site reports itself).
 void note_launches(int64_t n);
 int64_t launch_count();
+// Jacobi sweeps run on the block (shared-memory) schedule, and the last CUDA error
+// a cooperative launch returned (0 if none), for the statistics.
+void note_block_sweep(int err);
+int64_t block_sweep_count();
+int last_coop_error();
 
 #define FTT_CUDA(call) ::fasttt::cuda_check((call), #call, __FILE__, __LINE__)
 #define FTT_LAUNCH()                                                             \

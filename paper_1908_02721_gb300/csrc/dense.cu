@@ -298,6 +298,250 @@ __device__ __forceinline__ void jacobi_pair_warp(T* A, int64_t m, int64_t lda, T
   if (V) rotate_cols_warp<T, U>(V + (int64_t)p * ldv, V + (int64_t)q * ldv, nv, c, sn, lane);
 }
 
+// Block one-sided Jacobi: one sweep in one cooperative launch.  The columns are
+// cut into blocks of b; blocks meet by the circle schedule; a CTA owns a block
+// pair: it stages the 2b columns of A in shared memory (16-byte cp.async through
+// L2), runs one local sweep over all their pairs (wpp warps per pair), keeps
+// the local rotations in Q (2b x 2b), writes the columns back and multiplies
+// V's 2b columns by Q (4 x 4 register tiles over double-buffered chunks of V).
+// A block pair that rotated nothing skips the write-back and the V product.
+// Every pair of columns meets once per sweep, so a sweep without rotations
+// means convergence, as for the point schedule; rounds drop from n-1 to n/b-1.
+constexpr int kBlockJacobiMaxW = 32;   // 2b at most
+constexpr int kBlockJacobiMaxWpp = 4;  // warps per local pair at most
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ void dot3(const float4& x, const float4& y, float& a, float& b, float& g) {
+  a = fmaf(x.x, x.x, a); a = fmaf(x.y, x.y, a); a = fmaf(x.z, x.z, a); a = fmaf(x.w, x.w, a);
+  b = fmaf(y.x, y.x, b); b = fmaf(y.y, y.y, b); b = fmaf(y.z, y.z, b); b = fmaf(y.w, y.w, b);
+  g = fmaf(x.x, y.x, g); g = fmaf(x.y, y.y, g); g = fmaf(x.z, y.z, g); g = fmaf(x.w, y.w, g);
+}
+__device__ __forceinline__ void dot3(const double2& x, const double2& y, double& a, double& b, double& g) {
+  a = fma(x.x, x.x, a); a = fma(x.y, x.y, a);
+  b = fma(y.x, y.x, b); b = fma(y.y, y.y, b);
+  g = fma(x.x, y.x, g); g = fma(x.y, y.y, g);
+}
+__device__ __forceinline__ void rot2(float4& x, float4& y, float c, float s) {
+  const float4 u = x, v = y;
+  x = make_float4(c * u.x - s * v.x, c * u.y - s * v.y, c * u.z - s * v.z, c * u.w - s * v.w);
+  y = make_float4(s * u.x + c * v.x, s * u.y + c * v.y, s * u.z + c * v.z, s * u.w + c * v.w);
+}
+__device__ __forceinline__ void rot2(double2& x, double2& y, double c, double s) {
+  const double2 u = x, v = y;
+  x = make_double2(c * u.x - s * v.x, c * u.y - s * v.y);
+  y = make_double2(s * u.x + c * v.x, s * u.y + c * v.y);
+}
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// dst[0, len) <- src[0, len), read through L2 (another CTA may have written src
+// since this SM last read it): 16-byte cp.async when vec (both ends 16-byte
+// aligned), else loads through registers.  Completion: cp_async_commit + wait.
+template <typename T>
+__device__ __forceinline__ void stage_async(T* __restrict__ dst, const T* __restrict__ src, int len, bool vec) {
+  constexpr int W = Vec16<T>::n;
+  int done = 0;
+  if (vec) {
+    const int nvec = len / W;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) cp_async16(dst + i * W, src + i * W);
+    done = nvec * W;
+  }
+#pragma unroll 8
+  for (int i = done + threadIdx.x; i < len; i += blockDim.x) dst[i] = __ldcg(src + i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+    jacobi_block_sweep_kernel(T* A, int64_t m, int64_t lda, T* V, int64_t nv, int64_t ldv, int n, int b, int nb2,
+                              int wpp, int vrows, bool vec, T tol, T small2, unsigned* rotations, unsigned* bar) {
+  using VT = typename Vec16<T>::type;
+  constexpr int W = Vec16<T>::n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int cols[kBlockJacobiMaxW];
+  __shared__ T red[kBlockJacobiMaxW / 2][kBlockJacobiMaxWpp][3];
+  __shared__ int any_rot;
+  const int w2 = 2 * b, w2p = (w2 + 3) & ~3;
+  const int mv = (int)((m + W - 1) / W);   // 16-byte vectors per staged column (zero padded)
+  const int mp = mv * W;
+  T* As = reinterpret_cast<T*>(smem_raw);   // column c at As + c*mp
+  T* Qs = As + (size_t)w2 * mp;             // Q(k, c) at Qs[c*w2p + k]
+  T* QT = Qs + (size_t)w2 * w2p;            // Q(k, c) at QT[k*w2p + c]
+  T* Vb = QT + (size_t)w2 * w2p;            // two chunk buffers of V, [w2][vrows] each
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nthr = blockDim.x;
+  const int pair = warp / wpp, sub = warp % wpp;
+  unsigned gen = 0;
+  for (int round = 0; round < nb2 - 1; ++round) {
+    for (int pi = blockIdx.x; pi < nb2 / 2; pi += gridDim.x) {
+      int I, J;
+      if (pi == 0) { I = round; J = nb2 - 1; }
+      else { I = (round + pi) % (nb2 - 1); J = (round - pi + (nb2 - 1)) % (nb2 - 1); }
+      if (threadIdx.x < w2) {
+        const int c = threadIdx.x;
+        const int gc = ((c < b) ? I : J) * b + (c % b);
+        cols[c] = (gc < n) ? gc : -1;
+      }
+      if (threadIdx.x == 0) any_rot = 0;
+      __syncthreads();
+      for (int c = 0; c < w2; ++c) {
+        const int gc = cols[c];
+        T* dst = As + (size_t)c * mp;
+        if (gc >= 0) stage_async(dst, A + (int64_t)gc * lda, (int)m, vec);
+        for (int e = (gc >= 0 ? (int)m : 0) + threadIdx.x; e < mp; e += nthr) dst[e] = T(0);
+      }
+      cp_async_commit();
+      for (int e = threadIdx.x; e < w2 * w2p; e += nthr) Qs[e] = (e / w2p == e % w2p) ? T(1) : T(0);
+      cp_async_wait<0>();
+      __syncthreads();
+      for (int lr = 0; lr < w2 - 1; ++lr) {
+        int p = 0, q = 0;
+        bool act = false;
+        if (pair < b) {
+          if (pair == 0) { p = lr; q = w2 - 1; }
+          else { p = (lr + pair) % (w2 - 1); q = (lr - pair + (w2 - 1)) % (w2 - 1); }
+          if (p > q) { const int t = p; p = q; q = t; }
+          act = cols[p] >= 0 && cols[q] >= 0;
+        }
+        VT* ap = reinterpret_cast<VT*>(As + (size_t)p * mp);
+        VT* aq = reinterpret_cast<VT*>(As + (size_t)q * mp);
+        if (act) {
+          T al = 0, be = 0, ga = 0;
+          for (int i = sub * 32 + lane; i < mv; i += 32 * wpp) dot3(ap[i], aq[i], al, be, ga);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          }
+          if (lane == 0) { red[pair][sub][0] = al; red[pair][sub][1] = be; red[pair][sub][2] = ga; }
+        }
+        __syncthreads();
+        if (act) {
+          T al = 0, be = 0, ga = 0;
+          for (int u = 0; u < wpp; ++u) { al += red[pair][u][0]; be += red[pair][u][1]; ga += red[pair][u][2]; }
+          if (!(ga == T(0) || al <= small2 || be <= small2) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+            const T zeta = (be - al) / (T(2) * ga);
+            const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, T(1))));
+            const T c = T(1) / sqrt(fma(t, t, T(1)));
+            const T sn = c * t;
+            for (int i = sub * 32 + lane; i < mv; i += 32 * wpp) {
+              VT x = ap[i], y = aq[i];
+              rot2(x, y, c, sn);
+              ap[i] = x;
+              aq[i] = y;
+            }
+            if (sub == 0) {
+              if (lane < w2) {
+                T* qp = Qs + p * w2p;
+                T* qq = Qs + q * w2p;
+                const T x = qp[lane], y = qq[lane];
+                qp[lane] = c * x - sn * y;
+                qq[lane] = sn * x + c * y;
+              }
+              if (lane == 0) { atomicAdd(rotations, 1u); any_rot = 1; }
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (any_rot) {
+        for (int c = 0; c < w2; ++c) {
+          const int gc = cols[c];
+          if (gc < 0) continue;
+          T* dst = A + (int64_t)gc * lda;
+          const T* src = As + (size_t)c * mp;
+          int done = 0;
+          if (vec) {
+            const int full = (int)(m / W);
+            for (int i = threadIdx.x; i < full; i += nthr)
+              reinterpret_cast<VT*>(dst)[i] = reinterpret_cast<const VT*>(src)[i];
+            done = full * W;
+          }
+          for (int e = done + threadIdx.x; e < m; e += nthr) dst[e] = src[e];
+        }
+        for (int e = threadIdx.x; e < w2 * w2p; e += nthr) {
+          const int k = e / w2p, c = e % w2p;
+          QT[e] = (c < w2) ? Qs[c * w2p + k] : T(0);
+        }
+        if (V) {
+          const int nch = (int)((nv + vrows - 1) / vrows);
+          auto issue = [&](int ch) {
+            T* buf = Vb + (size_t)(ch & 1) * w2 * vrows;
+            const int64_t e0 = (int64_t)ch * vrows;
+            const int rows = (nv - e0 < vrows) ? (int)(nv - e0) : vrows;
+            for (int k = 0; k < w2; ++k) {
+              const int gk = cols[k];
+              T* dst = buf + (size_t)k * vrows;
+              if (gk >= 0) stage_async(dst, V + (int64_t)gk * ldv + e0, rows, vec);
+              else for (int r = threadIdx.x; r < vrows; r += nthr) dst[r] = T(0);
+            }
+            cp_async_commit();
+          };
+          issue(0);
+          for (int ch = 0; ch < nch; ++ch) {
+            if (ch + 1 < nch) { issue(ch + 1); cp_async_wait<1>(); }
+            else cp_async_wait<0>();
+            __syncthreads();
+            const T* buf = Vb + (size_t)(ch & 1) * w2 * vrows;
+            const int64_t e0 = (int64_t)ch * vrows;
+            const int rows = (nv - e0 < vrows) ? (int)(nv - e0) : vrows;
+            const int rq_n = (rows + 3) / 4, cq_n = w2p / 4;
+            for (int it = threadIdx.x; it < rq_n * cq_n; it += nthr) {
+              const int rq = it % rq_n, cq = it / rq_n;
+              T acc[4][4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+              for (int k = 0; k < w2; ++k) {
+                T v[4], qv[4];
+                load4(buf + (size_t)k * vrows + 4 * rq, v);
+                load4(QT + (size_t)k * w2p + 4 * cq, qv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) acc[i][j] = fma(v[i], qv[j], acc[i][j]);
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int c = 4 * cq + j;
+                const int gc = (c < w2) ? cols[c] : -1;
+                if (gc < 0) continue;
+                T* dst = V + (int64_t)gc * ldv + e0 + 4 * rq;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                  if (4 * rq + i < rows) dst[i] = acc[i][j];
+              }
+            }
+            __syncthreads();   // the buffer is refilled two chunks on
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, gridDim.x, gen)) return;
+  }
+}
+
 // A whole sweep in one cooperative launch, one warp per pair.
 template <typename T>
 __global__ void __launch_bounds__(256) jacobi_sweep_warp_kernel(T* A, int64_t m, int64_t lda, T* V, int64_t nv,
@@ -410,12 +654,75 @@ int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ld
   const int units_per_block = warp_pairs ? 8 : 1;
   const int coop_blocks = std::min((n2 / 2 + units_per_block - 1) / units_per_block, per_sm * sms);
   bool use_coop = coop && coop_blocks >= 1 && n2 / 2 > 1;
+  // block schedule (FP32 Gram eigenproblems): b columns per block so that the block
+  // pairs of a round fit on the SMs, 2b columns of A resident in shared memory
+  int bj = 0, nb2 = 0, bj_grid = 0, bj_wpp = 1, bj_vrows = 0;
+  bool bj_vec = false;
+  size_t bj_smem = 0;
+  if (!f64 && V && coop && n >= 64) {
+    int smem_max = 0;
+    FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t budget = (size_t)std::max(0, smem_max - 4096);   // static shared memory of the kernel below
+    constexpr int W = 16 / (int)sizeof(T);
+    const size_t mp = (size_t)ceil_div(m, W) * W;
+    auto bytes = [&](int b, int vrows) {
+      const size_t w2 = 2 * b, w2p = (w2 + 3) & ~(size_t)3;
+      return sizeof(T) * (w2 * mp + 2 * w2 * w2p + 2 * w2 * (size_t)vrows);
+    };
+    const int vr_cap = (int)std::min<int64_t>(512, (nv + 3) & ~(int64_t)3);
+    int b = (int)std::min<int64_t>(kBlockJacobiMaxW / 2, std::max<int64_t>(2, ceil_div(n, 2 * sms)));
+    int vrows = 0;
+    for (; b >= 2; --b) {
+      for (int vr = vr_cap; vr >= 4 && vrows == 0; vr = (vr > 64) ? vr / 2 : vr - 4)
+        if (bytes(b, vr & ~3) <= budget) vrows = vr & ~3;
+      if (vrows > 0) break;
+    }
+    if (b >= 2 && vrows >= 4) {
+      bj_wpp = std::max(1, std::min(kBlockJacobiMaxWpp, 32 / b));
+      bj_vrows = vrows;
+      bj_smem = bytes(b, vrows);
+      bj_vec = ((uintptr_t)A % 16 == 0) && ((uintptr_t)V % 16 == 0) && ((size_t)lda * sizeof(T)) % 16 == 0 &&
+               ((size_t)ldv * sizeof(T)) % 16 == 0;
+      FTT_CUDA(cudaFuncSetAttribute(jacobi_block_sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bj_smem));
+      int per = 0;
+      FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_block_sweep_kernel<T>, 32 * bj_wpp * b,
+                                                             bj_smem));
+      const int nb = (int)ceil_div(n, b);
+      nb2 = nb + (nb & 1);
+      bj_grid = std::min(nb2 / 2, per * sms);
+      if (bj_grid >= 1) bj = b;
+    }
+  }
   for (int64_t sweep = 1; sweep <= max_sweeps; ++sweep) {
     FTT_CUDA(cudaMemsetAsync(rot.get(), 0, 4 * sizeof(unsigned), s));
     KClock clk;
     kclock_begin(clk, f64 ? KC_JACOBI : KC_JACOBI32, s);
     bool done = false;
-    if (use_coop) {
+    if (bj > 0) {
+      unsigned* rp = rot.get();
+      unsigned* bp = rot.get() + 1;
+      void* args[] = {(void*)&A,   (void*)&m,      (void*)&lda,      (void*)&V,      (void*)&nv,
+                      (void*)&ldv, (void*)&n,      (void*)&bj,       (void*)&nb2,    (void*)&bj_wpp,
+                      (void*)&bj_vrows, (void*)&bj_vec, (void*)&tol, (void*)&small2, (void*)&rp,
+                      (void*)&bp};
+      cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_block_sweep_kernel<T>, dim3(bj_grid),
+                                                  dim3(32 * bj_wpp * bj), args, bj_smem, s);
+      note_block_sweep((int)e);
+      if (e == cudaSuccess) {
+        FTT_LAUNCH();
+        unsigned h[4];
+        FTT_CUDA(cudaMemcpyAsync(h, rot.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+        FTT_CUDA(cudaStreamSynchronize(s));
+        if (h[3] == 0) done = true;
+        else bj = 0;
+      } else {
+        cudaGetLastError();
+        bj = 0;
+      }
+      if (!done) FTT_CUDA(cudaMemsetAsync(rot.get(), 0, 4 * sizeof(unsigned), s));
+    }
+    if (!done && use_coop) {
       unsigned* rp = rot.get();
       unsigned* bp = rot.get() + 1;
       void* args[] = {(void*)&A, (void*)&m, (void*)&lda, (void*)&V, (void*)&nv, (void*)&ldv, (void*)&n,

@@ -55,6 +55,17 @@ thread_local std::vector<KClock> g_clocks;
 }  // namespace
 
 void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+std::atomic<int64_t> g_block_sweeps{0};
+std::atomic<int> g_coop_err{0};
+}  // namespace
+void note_block_sweep(int err) {
+  if (err) g_coop_err.store(err);
+  else g_block_sweeps.fetch_add(1, std::memory_order_relaxed);
+}
+int64_t block_sweep_count() { return g_block_sweeps.load(); }
+int last_coop_error() { return g_coop_err.load(); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void kclock_begin(KClock& c, int cls, cudaStream_t s) {
@@ -267,6 +278,11 @@ void finish_stats(fasttt_stats& st, int64_t launches0) {
   st.launches = launch_count() - launches0;
 }
 
+void finish_block_stats(fasttt_stats& st, int64_t bsweeps0) {
+  st.jacobi_block_sweeps = block_sweep_count() - bsweeps0;
+  st.coop_launch_error = last_coop_error();
+}
+
 double tail2(const std::vector<double>& s, int64_t r) {
   double acc = 0.0;
   for (int64_t i = (int64_t)s.size() - 1; i >= r; --i) acc += s[i] * s[i];
@@ -285,6 +301,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   st.d = d;
   kclock_reset();
   const int64_t launches0 = launch_count();
+  const int64_t bsweeps0 = block_sweep_count();
   Timer total(s), lap(s);
   // S1
   Ingested in;
@@ -514,6 +531,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   st.ms_round = lap.lap();
   st.ms_total = total.lap();
   finish_stats(st, launches0);
+  finish_block_stats(st, bsweeps0);
 }
 
 int handle_error(const Error& e) {

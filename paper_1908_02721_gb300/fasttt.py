@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("dropped", ctypes.c_int64), ("R", ctypes.c_int64), ("Rs", ctypes.c_int64 * MAX_D),
                 ("rt", ctypes.c_int64 * (MAX_D + 1)), ("ranks", ctypes.c_int64 * (MAX_D + 1)),
                 ("beta_r", ctypes.c_int64), ("beta_c", ctypes.c_int64), ("jacobi_sweeps", ctypes.c_int64),
-                ("launches", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("jacobi_block_sweeps", ctypes.c_int64),
+                ("coop_launch_error", ctypes.c_int64),
                 ("norm2", ctypes.c_double), ("err2", ctypes.c_double),
                 ("deltas", ctypes.c_double * (MAX_D + 1)), ("ms_ingest", ctypes.c_double),
                 ("ms_group", ctypes.c_double), ("ms_depar", ctypes.c_double), ("ms_round", ctypes.c_double),
@@ -65,7 +66,9 @@ class Stats(ctypes.Structure):
         return {"d": d, "p": self.p, "nnz_in": self.nnz_in, "nnz": self.nnz, "dropped": self.dropped,
                 "R": self.R, "Rs": list(self.Rs[:d]), "rt": list(self.rt[:d + 1]),
                 "ranks": list(self.ranks[:d + 1]), "beta_r": self.beta_r, "beta_c": self.beta_c,
-                "jacobi_sweeps": self.jacobi_sweeps, "launches": self.launches, "norm2": self.norm2,
+                "jacobi_sweeps": self.jacobi_sweeps, "launches": self.launches,
+                "jacobi_block_sweeps": self.jacobi_block_sweeps, "coop_launch_error": self.coop_launch_error,
+                "norm2": self.norm2,
                 "err2": self.err2,
                 "deltas": list(self.deltas[:d + 1]), "ms_ingest": self.ms_ingest, "ms_group": self.ms_group,
                 "ms_depar": self.ms_depar, "ms_round": self.ms_round, "ms_total": self.ms_total,
