@@ -75,10 +75,24 @@ typedef struct fasttt_opts {
   int keep_intermediates; /* 1: keep group maps, middle COO, Depar factors, singular values */
   int64_t max_rank;   /* > 0: cap every TT rank (fixed-rank variant, Sec. 3.4); 0: none */
   int64_t max_sweeps; /* Jacobi sweep bound of the dense SVDs; 0 = default (40) */
+  int sparse_sweep;   /* first SVD sweep (Alg. 6) bonds: FASTTT_SWEEP_AUTO, _SPARSE or _DENSE */
+  int reserved;       /* must be 0 */
 } fasttt_opts;
 
+/* How a bond k of the first SVD sweep sees G_k = W_{k-1} x_1 P_k (P_k the right
+ * quasi-permutation core of Alg. 4).  DENSE: G_k is materialised (r_{k-1} x n_k x
+ * r~_k) and its k-unfolding goes through the dense SVD.  SPARSE: G_k stays
+ * implicit (W_{k-1} and the group maps); the Gram Z Z^T of Z = unfold_2(G_k)
+ * ((r_{k-1} n_k)^2) and the projection U^T Z are formed from the nonzero blocks
+ * only, which is what makes r~_k in the millions feasible.  AUTO: SPARSE when the
+ * dense core would exceed 2 GiB and r_{k-1} n_k <= 16384, else DENSE.  SPARSE
+ * requested where r_{k-1} n_k > 16384 falls back to DENSE. */
+#define FASTTT_SWEEP_AUTO 0
+#define FASTTT_SWEEP_SPARSE 1
+#define FASTTT_SWEEP_DENSE 2
+
 /* Fills *opts with the defaults: p = 0, FP64, static rounding, value Depar on,
- * full stage, no intermediates, no rank cap, default sweep bound. */
+ * full stage, no intermediates, no rank cap, default sweep bound, AUTO sweep. */
 void fasttt_default_opts(fasttt_opts* opts);
 
 typedef struct fasttt_stats {
@@ -105,6 +119,7 @@ typedef struct fasttt_stats {
   double ms_gemm, flop_gemm, ms_jacobi, flop_jacobi, ms_sort, bytes_sort;
   double ms_jacobi32, flop_jacobi32; /* FP32 Jacobi sweeps (large eigenproblems) */
   double ms_gemm_tc, flop_gemm_tc;   /* split-TF32 tensor-core GEMMs (mixed precision) */
+  int64_t sparse_bonds;      /* first-sweep bonds run block-sparse (FASTTT_SWEEP_SPARSE path) */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */

@@ -95,15 +95,19 @@ __global__ void __launch_bounds__(256)
 __global__ void transpose_kernel(const double* __restrict__ src, int64_t rows, int64_t cols,
                                  double* __restrict__ dst) {
   __shared__ double t[32][33];
-  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int64_t r = r0 + j, c = c0 + threadIdx.x;
-    if (r < rows && c < cols) t[j][threadIdx.x] = src[r * cols + c];
-  }
-  __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int64_t c = c0 + j, r = r0 + threadIdx.x;
-    if (r < rows && c < cols) dst[c * rows + r] = t[threadIdx.x][j];
+  const int64_t c0 = (int64_t)blockIdx.x * 32;
+  // row tiles stride by gridDim.y (at most 65535 of them per launch)
+  for (int64_t r0 = (int64_t)blockIdx.y * 32; r0 < rows; r0 += (int64_t)gridDim.y * 32) {
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+      const int64_t r = r0 + j, c = c0 + threadIdx.x;
+      if (r < rows && c < cols) t[j][threadIdx.x] = src[r * cols + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+      const int64_t c = c0 + j, r = r0 + threadIdx.x;
+      if (r < rows && c < cols) dst[c * rows + r] = t[threadIdx.x][j];
+    }
+    __syncthreads();
   }
 }
 
@@ -1032,7 +1036,8 @@ void gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, in
 
 void transpose_f64(const double* src, int64_t rows, int64_t cols, double* dst, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return;
-  dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
+  if (ceil_div(cols, 32) > INT32_MAX) fail(FASTTT_ERANK, "transpose: too many columns");
+  dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)std::min<int64_t>(ceil_div(rows, 32), 65535));
   dim3 block(32, 8);
   transpose_kernel<<<grid, block, 0, s>>>(src, rows, cols, dst);
   FTT_LAUNCH();
@@ -1148,6 +1153,38 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
       FTT_LAUNCH();
     }
   }
+}
+
+void svd_from_gram(const double* Gram, int64_t M, int64_t N,
+                   const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
+                   SvdOut& out, cudaStream_t s, bool mixed) {
+  if (M > INT32_MAX / 2) fail(FASTTT_ERANK, "SVD too large");
+  const int n = (int)M;
+  DBuf<double> V((size_t)n * n, s);
+  std::vector<double> h(n);
+  out.sweeps = mixed ? sym_eig_mixed32(Gram, n, V.get(), h, max_sweeps, s)
+                     : sym_eig_refined(Gram, n, V.get(), h, max_sweeps, s);
+  for (auto& x : h) {
+    x = sqrt(std::max(x, 0.0));
+    if (!std::isfinite(x)) fail(FASTTT_ENUMERIC, "non-finite singular value");
+  }
+  std::vector<int32_t> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return h[a] > h[b]; });
+  const int nsv = (int)std::min<int64_t>(n, N);
+  out.sigma_all.resize(nsv);
+  for (int i = 0; i < nsv; ++i) out.sigma_all[i] = h[perm[i]];
+  int64_t r = choose_rank(out.sigma_all);
+  r = std::max<int64_t>(1, std::min<int64_t>(r, nsv));
+  out.r = r;
+  DBuf<int32_t> dperm(r, s);
+  out.sigma = DBuf<double>(r, s);
+  FTT_CUDA(cudaMemcpyAsync(dperm.get(), perm.data(), sizeof(int32_t) * r, cudaMemcpyHostToDevice, s));
+  FTT_CUDA(cudaMemcpyAsync(out.sigma.get(), out.sigma_all.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  out.U = DBuf<double>((size_t)M * r, s);
+  gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(V.get(), n, M, dperm.get(), nullptr, r, out.U.get());
+  FTT_LAUNCH();
+  FTT_CUDA(cudaStreamSynchronize(s));   // perm and sigma_all are host memory read by the copies above
 }
 
 }  // namespace fasttt

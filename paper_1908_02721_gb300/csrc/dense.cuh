@@ -52,4 +52,13 @@ struct SvdOut {
 void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<int64_t(const std::vector<double>&)>& choose_rank,
                    int64_t max_sweeps, SvdOut& out, cudaStream_t s, bool mixed = false, int ortho = 0);
 
+// The left singular factor of a matrix Z (M x N) given only its Gram Z Z^T
+// (M x M, symmetric): eigenvectors of the Gram as in svd_truncated's Gram route,
+// the min(M, N) singular values sqrt(max(lambda, 0)) descending (the other
+// eigenvalues are zero), r = choose_rank of those.
+// Fills out.r, out.sigma_all, out.sigma and out.U (M x r); out.Vt stays empty.
+void svd_from_gram(const double* Gram, int64_t M, int64_t N,
+                   const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
+                   SvdOut& out, cudaStream_t s, bool mixed = false);
+
 }  // namespace fasttt

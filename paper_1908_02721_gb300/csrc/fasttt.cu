@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "dense.cuh"
+#include "sparse_sweep.cuh"
 #include "depar.cuh"
 #include "group.cuh"
 
@@ -112,6 +113,11 @@ namespace {
 #define GRID_STRIDE(i, n)                                                            \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
        i += (int64_t)gridDim.x * blockDim.x)
+
+// first-sweep bonds: the implicit (block-sparse) core when the dense one would
+// exceed kDenseCoreBytes and its Gram side r_{k-1} n_k stays within kSparseGramMax
+constexpr double kDenseCoreBytes = 2.0 * 1024 * 1024 * 1024;
+constexpr int64_t kSparseGramMax = 16384;
 
 // ---------------------------------------------------------------- factor kernels
 
@@ -296,6 +302,8 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   if (o.precision != FASTTT_PREC_FP64 && o.precision != FASTTT_PREC_MIXED) fail(FASTTT_EINVAL, "unsupported precision");
   const bool mixed = (o.precision == FASTTT_PREC_MIXED);
   if (o.stage != FASTTT_STAGE_FULL && o.stage != FASTTT_STAGE_EXACT) fail(FASTTT_EINVAL, "bad stage");
+  if (o.sparse_sweep < FASTTT_SWEEP_AUTO || o.sparse_sweep > FASTTT_SWEEP_DENSE || o.reserved != 0)
+    fail(FASTTT_EINVAL, "bad sparse_sweep mode");
   const int64_t max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
   fasttt_stats& st = H.st;
   st.d = d;
@@ -355,6 +363,15 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   for (int k = 0; k <= d; ++k) r[k] = g.rt[k];
   std::vector<DBuf<double>> G(d + 1);  // 1-based dense cores
   DBuf<double> UC;                      // G_p = Q_S UC while G[p] is empty (p < d)
+  // first-sweep core G_k (k > p) held implicitly: G_k = Wk x_1 P_k while G[k] is empty
+  DBuf<double> Wk;
+  auto keep_sparse = [&](int k, int64_t rp) {
+    if (k >= d) return false;   // the last core (r~_d = 1) is always small
+    if ((double)rp * (double)n[k - 1] > (double)kSparseGramMax) return false;
+    if (o.sparse_sweep == FASTTT_SWEEP_SPARSE) return true;
+    if (o.sparse_sweep == FASTTT_SWEEP_DENSE) return false;
+    return (double)rp * (double)n[k - 1] * (double)g.rt[k] * 8.0 > kDenseCoreBytes;
+  };
   auto expand_Q_S = [&](const double* U, int64_t rr) {
     DBuf<double> X((size_t)g.mid_rows * rr, s);
     FTT_CUDA(cudaMemsetAsync(X.get(), 0, X.bytes(), s));
@@ -408,12 +425,16 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
       // G_p := U_X (held as U_C) ; G_{p+1} := G_{p+1} x_1 (Sigma V^T)  (right quasi-permutation core)
       r[p] = rr;
       const int k1 = p + 1;
-      DBuf<double> Gn((size_t)rr * n[k1 - 1] * r[k1], s);
-      FTT_CUDA(cudaMemsetAsync(Gn.get(), 0, Gn.bytes(), s));
-      merge_right_kernel<<<grid_for(rr * g.rt[p]), 256, 0, s>>>(SW.get(), rr, g.rt[p], g.right_index[0].get(),
-                                                                 g.right_child[0].get(), n[k1 - 1], r[k1], Gn.get());
-      FTT_LAUNCH();
-      G[k1] = std::move(Gn);
+      if (keep_sparse(k1, rr)) {
+        Wk = std::move(SW);
+      } else {
+        DBuf<double> Gn((size_t)rr * n[k1 - 1] * r[k1], s);
+        FTT_CUDA(cudaMemsetAsync(Gn.get(), 0, Gn.bytes(), s));
+        merge_right_kernel<<<grid_for(rr * g.rt[p]), 256, 0, s>>>(SW.get(), rr, g.rt[p], g.right_index[0].get(),
+                                                                   g.right_child[0].get(), n[k1 - 1], r[k1], Gn.get());
+        FTT_LAUNCH();
+        G[k1] = std::move(Gn);
+      }
       if (o.rounding == FASTTT_DYNAMIC) d_right = std::sqrt(std::max(d_right * d_right - e2, 0.0));
     } else {
       // p = d: G_d := U_X^T (r x n_d x 1); G_{d-1} := G_{d-1} x_3 (V Sigma) (left quasi-permutation core)
@@ -439,24 +460,43 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
     for (int k = p + 1; k <= d - 1; ++k) {
       const int64_t M = r[k - 1] * n[k - 1], N = r[k];
       const double dl = delta_for(k, true);
+      auto choose = [&](const std::vector<double>& sg) { return rank_rule(sg, dl, eps0, n, k, o.max_rank); };
       SvdOut sv;
-      svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) {
-        return rank_rule(sg, dl, eps0, n, k, o.max_rank);
-      }, max_sweeps, sv, s, mixed, 1);
+      DBuf<double> W;
+      if (!G[k].get()) {
+        // block-sparse bond: Gram and projection from W_{k-1} and the maps of P_k
+        SparseBond sb(Wk.get(), r[k - 1], g.rt[k - 1], g.right_index[k - p - 1].get(), g.right_child[k - p - 1].get(),
+                      n[k - 1], N, s);
+        Wk.reset();
+        {
+          DBuf<double> Gram((size_t)M * M, s);
+          sb.gram(Gram.get(), s);
+          svd_from_gram(Gram.get(), M, N, choose, max_sweeps, sv, s, mixed);
+        }
+        sb.project(sv.U.get(), sv.r, W, s);   // W_k = U^T Z = Sigma V^T
+        ++st.sparse_bonds;
+      } else {
+        svd_truncated(G[k].get(), M, N, choose, max_sweeps, sv, s, mixed, 1);
+        W = DBuf<double>((size_t)sv.r * N, s);
+        scale_rows_kernel<<<grid_for(sv.r * N), 256, 0, s>>>(sv.Vt.get(), sv.r, N, sv.sigma.get(), W.get());
+        FTT_LAUNCH();
+      }
       const double e2 = record(k, sv, dl);
       const int64_t rr = sv.r;
       G[k] = std::move(sv.U);
-      DBuf<double> W((size_t)rr * N, s);
-      scale_rows_kernel<<<grid_for(rr * N), 256, 0, s>>>(sv.Vt.get(), rr, N, sv.sigma.get(), W.get());
-      FTT_LAUNCH();
       r[k] = rr;
       const int k1 = k + 1;
-      DBuf<double> Gn((size_t)rr * n[k1 - 1] * r[k1], s);
-      FTT_CUDA(cudaMemsetAsync(Gn.get(), 0, Gn.bytes(), s));
-      merge_right_kernel<<<grid_for(rr * g.rt[k]), 256, 0, s>>>(W.get(), rr, g.rt[k], g.right_index[k - p].get(),
-                                                                 g.right_child[k - p].get(), n[k1 - 1], r[k1], Gn.get());
-      FTT_LAUNCH();
-      G[k1] = std::move(Gn);
+      if (keep_sparse(k1, rr)) {
+        Wk = std::move(W);
+      } else {
+        DBuf<double> Gn((size_t)rr * n[k1 - 1] * r[k1], s);
+        FTT_CUDA(cudaMemsetAsync(Gn.get(), 0, Gn.bytes(), s));
+        merge_right_kernel<<<grid_for(rr * g.rt[k]), 256, 0, s>>>(W.get(), rr, g.rt[k], g.right_index[k - p].get(),
+                                                                   g.right_child[k - p].get(), n[k1 - 1], r[k1],
+                                                                   Gn.get());
+        FTT_LAUNCH();
+        G[k1] = std::move(Gn);
+      }
       if (o.rounding == FASTTT_DYNAMIC) d_right = std::sqrt(std::max(d_right * d_right - e2, 0.0));
     }
     // --- QR sweep k = d..p+1: unfold_1^T(G_k) = Q R by an untruncated SVD of

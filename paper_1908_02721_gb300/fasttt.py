@@ -26,6 +26,7 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STATIC, DYNAMIC = 0, 1
 STAGE_FULL, STAGE_EXACT = 0, 1
+SWEEP_MODES = {"auto": 0, "sparse": 1, "dense": 2}
 ARR = {name: i for i, name in enumerate([
     "core", "left_parent", "left_index", "right_index", "right_child", "mid_row", "mid_col", "mid_val",
     "row_id", "row_class", "row_pref", "col_id", "col_class", "col_pref", "dp_row", "dp_col", "dp_val",
@@ -42,7 +43,8 @@ _ARR_DTYPE = {"core": torch.float64, "left_parent": torch.int32, "left_index": t
 class Opts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("rounding", ctypes.c_int),
                 ("depar_values", ctypes.c_int), ("stage", ctypes.c_int), ("keep_intermediates", ctypes.c_int),
-                ("max_rank", ctypes.c_int64), ("max_sweeps", ctypes.c_int64)]
+                ("max_rank", ctypes.c_int64), ("max_sweeps", ctypes.c_int64), ("sparse_sweep", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -59,7 +61,7 @@ class Stats(ctypes.Structure):
                 ("ms_jacobi", ctypes.c_double), ("flop_jacobi", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("bytes_sort", ctypes.c_double), ("ms_jacobi32", ctypes.c_double),
                 ("flop_jacobi32", ctypes.c_double), ("ms_gemm_tc", ctypes.c_double),
-                ("flop_gemm_tc", ctypes.c_double)]
+                ("flop_gemm_tc", ctypes.c_double), ("sparse_bonds", ctypes.c_int64)]
 
     def to_dict(self):
         d = self.d
@@ -75,7 +77,8 @@ class Stats(ctypes.Structure):
                 "ms_gemm": self.ms_gemm, "flop_gemm": self.flop_gemm, "ms_jacobi": self.ms_jacobi,
                 "flop_jacobi": self.flop_jacobi, "ms_sort": self.ms_sort, "bytes_sort": self.bytes_sort,
                 "ms_jacobi32": self.ms_jacobi32, "flop_jacobi32": self.flop_jacobi32,
-                "ms_gemm_tc": self.ms_gemm_tc, "flop_gemm_tc": self.flop_gemm_tc}
+                "ms_gemm_tc": self.ms_gemm_tc, "flop_gemm_tc": self.flop_gemm_tc,
+                "sparse_bonds": self.sparse_bonds}
 
 
 _P = ctypes.c_void_p
@@ -194,8 +197,11 @@ class TT:
 
 
 def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True, rounding="static",
-                     stage="full", keep_intermediates=False, max_sweeps=0, precision="fp64", stream=None) -> TT:
-    """FastTT (Alg. 7) of the COO tensor (idx (d, nnz) int32, vals float64/float32)."""
+                     stage="full", keep_intermediates=False, max_sweeps=0, precision="fp64", sparse_sweep="auto",
+                     stream=None) -> TT:
+    """FastTT (Alg. 7) of the COO tensor (idx (d, nnz) int32, vals float64/float32).
+
+    sparse_sweep: "auto", "sparse" or "dense", how the first SVD sweep holds its cores."""
     _require_cuda()
     idx = _dev(idx, torch.int32)
     if isinstance(vals, np.ndarray):
@@ -215,6 +221,9 @@ def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True
     o.keep_intermediates = 1 if keep_intermediates else 0
     o.max_sweeps = int(max_sweeps)
     o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+    if sparse_sweep not in SWEEP_MODES:
+        raise FastTTError(EINVAL, "sparse_sweep must be 'auto', 'sparse' or 'dense'")
+    o.sparse_sweep = SWEEP_MODES[sparse_sweep]
     out = ctypes.c_void_p(0)
     st = Stats()
     rc = _lib.fasttt_decompose(d, _i64arr(dims), int(idx.shape[1]), ctypes.c_void_p(idx.data_ptr()),

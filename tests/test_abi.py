@@ -45,9 +45,10 @@ def test_binding_loads_and_matches_exports(lib):
 
 def test_struct_layouts_match_header(lib):
     from paper_1908_02721_gb300 import fasttt as F
-    # fasttt_opts: six ints then two int64; fasttt_stats ends with the kernel-class doubles
-    assert ctypes.sizeof(F.Opts) == 6 * 4 + 2 * 8
-    assert F.Stats.flop_gemm_tc.offset + 8 == ctypes.sizeof(F.Stats)
+    # fasttt_opts: six ints, two int64, two ints; fasttt_stats ends with the kernel-class doubles
+    assert ctypes.sizeof(F.Opts) == 8 * 4 + 2 * 8
+    assert F.Opts.sparse_sweep.offset == 6 * 4 + 2 * 8
+    assert F.Stats.sparse_bonds.offset + 8 == ctypes.sizeof(F.Stats)
 
 
 def test_calls_without_gpu_fail_loudly(lib):
