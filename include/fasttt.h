@@ -120,6 +120,10 @@ typedef struct fasttt_stats {
   double ms_jacobi32, flop_jacobi32; /* FP32 Jacobi sweeps (large eigenproblems) */
   double ms_gemm_tc, flop_gemm_tc;   /* split-TF32 tensor-core GEMMs (mixed precision) */
   int64_t sparse_bonds;      /* first-sweep bonds run block-sparse (FASTTT_SWEEP_SPARSE path) */
+  double ms_tridiag, flop_tridiag; /* Householder tridiagonalisation of Gram matrices (2 n^3 flops) */
+  double ms_tdeig;           /* bisection + inverse iteration on the tridiagonal matrices */
+  int64_t eig_tridiag;       /* Gram eigenproblems solved by the tridiagonal route */
+  int64_t eig_fallbacks;     /* Gram eigenproblems handed to the iterative (Jacobi) eigensolver */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */
@@ -253,6 +257,17 @@ const char* fasttt_version(void);
 /* Test hook for the host-side failure paths: the n-th device allocation from now
  * (n >= 1) fails with ENOMEM; n = 0 disables it.  Affects the calling process. */
 void fasttt_debug_fail_alloc_after(int64_t n);
+
+/* Test hook for the dense eigensolver of the rounding SVDs (the paper has no
+ * counterpart; it exposes the Gram eigendecomposition of S7-S10 so that it can
+ * be checked on matrices with chosen spectra).  d_G: symmetric n x n FP64,
+ * row-major, device, read only.  d_V: n x n device output, eigenvector j in
+ * d_V[j*n .. j*n + n).  h_lam: n host doubles, eigenvalue j (unordered).
+ * method 0: Householder tridiagonalisation + bisection + inverse iteration
+ * only (FASTTT_ENUMERIC when that route declines); 1: FP32 Jacobi start +
+ * Ogita-Aishima refinement + FP64 Jacobi polish only; 2: 0, else 1 (what the
+ * library uses).  stream: cudaStream_t or NULL; returns after synchronising it. */
+int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_lam, int method, void* stream);
 
 #ifdef __cplusplus
 }

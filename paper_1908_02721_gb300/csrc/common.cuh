@@ -40,6 +40,7 @@ int64_t launch_count();
 void note_block_sweep(int err);
 int64_t block_sweep_count();
 int last_coop_error();
+void note_eig(bool tridiag);   // Gram eigensolver: tridiagonal route taken, or the iterative fallback
 
 #define FTT_CUDA(call) ::fasttt::cuda_check((call), #call, __FILE__, __LINE__)
 #define FTT_LAUNCH()                                                             \
@@ -50,7 +51,16 @@ int last_coop_error();
 
 // Per-call device timing of the heavy kernel classes, by CUDA events on the
 // launching stream (read once at the end of a call).
-enum KernelClass { KC_GEMM = 0, KC_JACOBI = 1, KC_SORT = 2, KC_JACOBI32 = 3, KC_GEMM_TC = 4, KC_COUNT = 5 };
+enum KernelClass {
+  KC_GEMM = 0,
+  KC_JACOBI = 1,
+  KC_SORT = 2,
+  KC_JACOBI32 = 3,
+  KC_GEMM_TC = 4,
+  KC_TRIDIAG = 5,   // Householder tridiagonalisation
+  KC_TDEIG = 6,     // bisection + inverse iteration on the tridiagonal matrix
+  KC_COUNT = 7
+};
 struct KClock {
   cudaEvent_t a = nullptr, b = nullptr;
   int cls = 0;

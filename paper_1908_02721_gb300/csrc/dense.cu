@@ -21,6 +21,7 @@
 #include <numeric>
 
 #include "dense.cuh"
+#include "devsync.cuh"
 
 namespace fasttt {
 
@@ -115,28 +116,6 @@ __global__ void identity_kernel(double* V, int64_t n) {
   GRID_STRIDE(i, n * n) V[i] = ((i / n) == (i % n)) ? 1.0 : 0.0;
 }
 
-// Block-wide sum of three values (256 threads).
-template <typename T>
-__device__ __forceinline__ void block_sum3(T& a, T& b, T& c) {
-  __shared__ T red[3][8];
-  __syncthreads();  // earlier readers of red are done
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    T x = 0, y = 0, z = 0;
-    for (int w = 0; w < 8; ++w) { x += red[0][w]; y += red[1][w]; z += red[2][w]; }
-    red[0][0] = x; red[1][0] = y; red[2][0] = z;
-  }
-  __syncthreads();
-  a = red[0][0]; b = red[1][0]; c = red[2][0];
-}
 
 template <bool kCoherent, typename T>
 __device__ __forceinline__ T ld(const T* p) {
@@ -195,41 +174,7 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(T* A, int64_t m, int6
   jacobi_pair<false, T>(A, m, lda, V, nv, ldv, n, n2, round, blockIdx.x, tol, small2, rotations);
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  bar[0]
-// counts arrivals, bar[1] is the generation, bar[2] an error flag.  The wait is
-// bounded: after kBarrierSpins polls the block raises the error flag and every
-// block leaves the kernel at its next barrier.
-constexpr long long kBarrierSpins = 1ll << 24;
 constexpr int64_t kWarpPairMax = 16384;
-
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen) {
-  __shared__ int ok;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* vgen = bar + 1;
-    volatile unsigned* verr = bar + 2;
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long it = 0;
-      while (*vgen == gen) {
-        if (*verr) { ok = 0; break; }
-        if (++it > kBarrierSpins) { atomicOr(bar + 2, 1u); ok = 0; break; }
-        __nanosleep(64);
-      }
-    }
-    if (*verr) ok = 0;
-    __threadfence();
-  }
-  __syncthreads();
-  ++gen;
-  return ok != 0;
-}
 
 // (a, b) <- (c a - s b, s a + c b) over n elements, U loads per lane in flight
 template <typename T, int U>
@@ -1082,8 +1027,11 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
     FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
   } else {
-    out.sweeps = mixed ? sym_eig_mixed32(A.get(), n, V.get(), h, max_sweeps, s)
-                       : sym_eig_refined(A.get(), n, V.get(), h, max_sweeps, s);
+    const bool td = sym_eig_tridiag(A.get(), n, V.get(), h, s, mixed);
+    note_eig(td);
+    if (td) out.sweeps = 0;
+    else out.sweeps = mixed ? sym_eig_mixed32(A.get(), n, V.get(), h, max_sweeps, s)
+                            : sym_eig_refined(A.get(), n, V.get(), h, max_sweeps, s);
     for (auto& x : h) x = sqrt(std::max(x, 0.0));  // eigenvalues of the Gram -> singular values
   }
   for (double x : h)
@@ -1155,6 +1103,11 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
   }
 }
 
+void sym_eig_iterative(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps,
+                       cudaStream_t s) {
+  sym_eig_refined(G, n, V, lam_out, max_sweeps, s);
+}
+
 void svd_from_gram(const double* Gram, int64_t M, int64_t N,
                    const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
                    SvdOut& out, cudaStream_t s, bool mixed) {
@@ -1162,8 +1115,11 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
   const int n = (int)M;
   DBuf<double> V((size_t)n * n, s);
   std::vector<double> h(n);
-  out.sweeps = mixed ? sym_eig_mixed32(Gram, n, V.get(), h, max_sweeps, s)
-                     : sym_eig_refined(Gram, n, V.get(), h, max_sweeps, s);
+  const bool td = sym_eig_tridiag(Gram, n, V.get(), h, s, mixed);
+  note_eig(td);
+  if (td) out.sweeps = 0;
+  else out.sweeps = mixed ? sym_eig_mixed32(Gram, n, V.get(), h, max_sweeps, s)
+                          : sym_eig_refined(Gram, n, V.get(), h, max_sweeps, s);
   for (auto& x : h) {
     x = sqrt(std::max(x, 0.0));
     if (!std::isfinite(x)) fail(FASTTT_ENUMERIC, "non-finite singular value");

@@ -52,6 +52,18 @@ struct SvdOut {
 void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<int64_t(const std::vector<double>&)>& choose_rank,
                    int64_t max_sweeps, SvdOut& out, cudaStream_t s, bool mixed = false, int ortho = 0);
 
+// Eigendecomposition of the symmetric n x n G (row-major FP64) by Householder
+// tridiagonalisation, bisection and inverse iteration (tridiag.cu).  V (n x n)
+// receives eigenvector j in V[j*n .. j*n + n), lam_out the eigenvalues.  mixed:
+// the back-transformation GEMMs run split-TF32.  Returns false (V undefined)
+// when the route does not apply or its vectors could not be made orthonormal.
+bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed);
+
+// The iterative eigensolver of the Gram route (FP32 Jacobi start, Ogita-Aishima
+// refinement, FP64 one-sided Jacobi polish); same layout as sym_eig_tridiag.
+void sym_eig_iterative(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps,
+                       cudaStream_t s);
+
 // The left singular factor of a matrix Z (M x N) given only its Gram Z Z^T
 // (M x M, symmetric): eigenvectors of the Gram as in svd_truncated's Gram route,
 // the min(M, N) singular values sqrt(max(lambda, 0)) descending (the other

@@ -60,7 +60,9 @@ void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxe
 namespace {
 std::atomic<int64_t> g_block_sweeps{0};
 std::atomic<int> g_coop_err{0};
+std::atomic<int64_t> g_eig_tridiag{0}, g_eig_fallback{0};
 }  // namespace
+void note_eig(bool tridiag) { (tridiag ? g_eig_tridiag : g_eig_fallback).fetch_add(1, std::memory_order_relaxed); }
 void note_block_sweep(int err) {
   if (err) g_coop_err.store(err);
   else g_block_sweeps.fetch_add(1, std::memory_order_relaxed);
@@ -280,13 +282,22 @@ void finish_stats(fasttt_stats& st, int64_t launches0) {
   st.flop_jacobi32 = work[KC_JACOBI32];
   st.ms_gemm_tc = ms[KC_GEMM_TC];
   st.flop_gemm_tc = work[KC_GEMM_TC];
+  st.ms_tridiag = ms[KC_TRIDIAG];
+  st.flop_tridiag = work[KC_TRIDIAG];
+  st.ms_tdeig = ms[KC_TDEIG];
   kclock_reset();
   st.launches = launch_count() - launches0;
 }
 
-void finish_block_stats(fasttt_stats& st, int64_t bsweeps0) {
-  st.jacobi_block_sweeps = block_sweep_count() - bsweeps0;
+struct CounterSnap {
+  int64_t block_sweeps, eig_tridiag, eig_fallback;
+};
+CounterSnap counter_snap() { return {block_sweep_count(), g_eig_tridiag.load(), g_eig_fallback.load()}; }
+void finish_block_stats(fasttt_stats& st, const CounterSnap& c0) {
+  st.jacobi_block_sweeps = block_sweep_count() - c0.block_sweeps;
   st.coop_launch_error = last_coop_error();
+  st.eig_tridiag = g_eig_tridiag.load() - c0.eig_tridiag;
+  st.eig_fallbacks = g_eig_fallback.load() - c0.eig_fallback;
 }
 
 double tail2(const std::vector<double>& s, int64_t r) {
@@ -309,7 +320,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   st.d = d;
   kclock_reset();
   const int64_t launches0 = launch_count();
-  const int64_t bsweeps0 = block_sweep_count();
+  const CounterSnap snap0 = counter_snap();
   Timer total(s), lap(s);
   // S1
   Ingested in;
@@ -571,7 +582,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   st.ms_round = lap.lap();
   st.ms_total = total.lap();
   finish_stats(st, launches0);
-  finish_block_stats(st, bsweeps0);
+  finish_block_stats(st, snap0);
 }
 
 int handle_error(const Error& e) {
@@ -774,6 +785,24 @@ const char* fasttt_version(void) { return "fasttt-gb300 0.1 (sm_103a)"; }
 void fasttt_debug_fail_alloc_after(int64_t n) {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
   g_fail_after = n > 0 ? n : 0;
+}
+
+int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_lam, int method, void* stream) {
+  try {
+    if (!d_G || !d_V || !h_lam || n < 1 || n > INT32_MAX / 2 || method < 0 || method > 2)
+      fail(FASTTT_EINVAL, "fasttt_debug_sym_eig: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<double> lam;
+    bool ok = false;
+    if (method != 1) ok = sym_eig_tridiag(d_G, (int)n, d_V, lam, s, false);
+    if (!ok && method == 0) fail(FASTTT_ENUMERIC, "tridiagonal route declined");
+    if (!ok) sym_eig_iterative(d_G, (int)n, d_V, lam, 40, s);
+    FTT_CUDA(cudaStreamSynchronize(s));
+    std::copy(lam.begin(), lam.end(), h_lam);
+    return FASTTT_OK;
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
 }
 
 }  // extern "C"

@@ -61,7 +61,9 @@ class Stats(ctypes.Structure):
                 ("ms_jacobi", ctypes.c_double), ("flop_jacobi", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("bytes_sort", ctypes.c_double), ("ms_jacobi32", ctypes.c_double),
                 ("flop_jacobi32", ctypes.c_double), ("ms_gemm_tc", ctypes.c_double),
-                ("flop_gemm_tc", ctypes.c_double), ("sparse_bonds", ctypes.c_int64)]
+                ("flop_gemm_tc", ctypes.c_double), ("sparse_bonds", ctypes.c_int64),
+                ("ms_tridiag", ctypes.c_double), ("flop_tridiag", ctypes.c_double), ("ms_tdeig", ctypes.c_double),
+                ("eig_tridiag", ctypes.c_int64), ("eig_fallbacks", ctypes.c_int64)]
 
     def to_dict(self):
         d = self.d
@@ -78,7 +80,9 @@ class Stats(ctypes.Structure):
                 "flop_jacobi": self.flop_jacobi, "ms_sort": self.ms_sort, "bytes_sort": self.bytes_sort,
                 "ms_jacobi32": self.ms_jacobi32, "flop_jacobi32": self.flop_jacobi32,
                 "ms_gemm_tc": self.ms_gemm_tc, "flop_gemm_tc": self.flop_gemm_tc,
-                "sparse_bonds": self.sparse_bonds}
+                "sparse_bonds": self.sparse_bonds, "ms_tridiag": self.ms_tridiag,
+                "flop_tridiag": self.flop_tridiag, "ms_tdeig": self.ms_tdeig, "eig_tridiag": self.eig_tridiag,
+                "eig_fallbacks": self.eig_fallbacks}
 
 
 _P = ctypes.c_void_p
@@ -102,11 +106,12 @@ _lib.tt_eval_backward_noalloc.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POI
 _lib.fasttt_last_error.restype = ctypes.c_char_p
 _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
+_lib.fasttt_debug_sym_eig.argtypes = [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, _P]
 
 EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_tt_stats", "fasttt_tt_ranks",
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
            "tt_eval_backward_noalloc",
-           "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after"]
+           "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig"]
 
 
 class FastTTError(RuntimeError):
@@ -126,6 +131,27 @@ def version() -> str:
 
 def debug_fail_alloc_after(n: int) -> None:
     _lib.fasttt_debug_fail_alloc_after(int(n))
+
+
+EIG_METHODS = {"tridiagonal": 0, "iterative": 1, "auto": 2}
+
+
+def debug_sym_eig(G, method="auto", stream=None):
+    """Eigendecomposition of the symmetric FP64 CUDA matrix G through the library's
+    Gram eigensolver (a test hook).  Returns (lam (n,) numpy, V (n, n) torch) with
+    V[j] the eigenvector of lam[j]."""
+    _require_cuda()
+    G = _dev(G, torch.float64)
+    n = int(G.shape[0])
+    if G.dim() != 2 or G.shape[1] != n:
+        raise FastTTError(EINVAL, "G must be square")
+    V = torch.empty((n, n), dtype=torch.float64, device=G.device)
+    lam = np.zeros(n, dtype=np.float64)
+    rc = _lib.fasttt_debug_sym_eig(ctypes.c_void_p(G.data_ptr()), n, ctypes.c_void_p(V.data_ptr()),
+                                   lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), EIG_METHODS[method],
+                                   _stream(stream))
+    _check(rc)
+    return lam, V
 
 
 def _require_cuda():
