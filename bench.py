@@ -212,7 +212,8 @@ def run_ours(args):
     st = stats[-1]
     peaks, src = _peaks()
     # dominant kernel class by device time
-    classes = {"gemm_f64": (st["ms_gemm"], st["flop_gemm"]), "jacobi_f64": (st["ms_jacobi"], st["flop_jacobi"])}
+    classes = {"gemm_f64": (st["ms_gemm"], st["flop_gemm"]), "jacobi_f64": (st["ms_jacobi"], st["flop_jacobi"]),
+               "tridiag_f64": (st["ms_tridiag"], st["flop_tridiag"])}
     name, (kms, kwork) = max(classes.items(), key=lambda kv: kv[1][0])
     achieved = kwork / (kms / 1e3) / 1e12 if kms > 0 else 0.0
     roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -241,7 +242,8 @@ def run_ours(args):
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm",
-                                              "ms_jacobi", "ms_jacobi32", "ms_sort")},
+                                              "ms_jacobi", "ms_tridiag", "ms_tdeig", "ms_jacobi32", "ms_sort")},
+            "gram_eigensolver": {"tridiagonal": st["eig_tridiag"], "iterative_fallback": st["eig_fallbacks"]},
             "jacobi_sweeps": st["jacobi_sweeps"],
             "wall_s": wall, "peaks_source": src}
     print(json.dumps(line), flush=True)
@@ -289,7 +291,8 @@ def _mixed(args, F, idx, vals, w, flush, stream):
     return {"value": w.nnz / (ms / 1e3), "unit": "nnz/s", "ms_per_step": ms, "rel_err_sampled": err,
             "ranks": st["ranks"], "dtype": "tf32x3 tensor-core contractions + f32/f64",
             "tensor_gemm": {"ms": tc, "tflops": st["flop_gemm_tc"] / (tc / 1e3) / 1e12 if tc else None},
-            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_tc", "ms_jacobi", "ms_jacobi32")}}
+            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_tc", "ms_gemm", "ms_jacobi", "ms_tridiag",
+                                              "ms_tdeig", "ms_jacobi32")}}
 
 
 def _adjoint(args, F, dev, stream):
