@@ -76,8 +76,17 @@ typedef struct fasttt_opts {
   int64_t max_rank;   /* > 0: cap every TT rank (fixed-rank variant, Sec. 3.4); 0: none */
   int64_t max_sweeps; /* Jacobi sweep bound of the dense SVDs; 0 = default (40) */
   int sparse_sweep;   /* first SVD sweep (Alg. 6) bonds: FASTTT_SWEEP_AUTO, _SPARSE or _DENSE */
-  int reserved;       /* must be 0 */
+  int gemm_engine;    /* FASTTT_GEMM_TENSOR (default) or FASTTT_GEMM_DFMA */
 } fasttt_opts;
+
+/* Engine of the dense FP64 contractions.  TENSOR: products of at least 2^26
+ * multiply-adds run on the tcgen05 tensor cores from exact bf16 slices of the
+ * FP64 operands (7 slices: every slice product exact, FP64 accumulation of the
+ * exact FP32 partial sums; FP64-level results, Ozaki-Ogita-Oishi-Rump splitting),
+ * smaller ones on FP64 DFMA.  DFMA: every FP64 product on FP64 DFMA.  In mixed
+ * precision, TENSOR runs the large products from 3 slices (FP32-level). */
+#define FASTTT_GEMM_TENSOR 0
+#define FASTTT_GEMM_DFMA 1
 
 /* How a bond k of the first SVD sweep sees G_k = W_{k-1} x_1 P_k (P_k the right
  * quasi-permutation core of Alg. 4).  DENSE: G_k is materialised (r_{k-1} x n_k x
@@ -124,6 +133,7 @@ typedef struct fasttt_stats {
   double ms_tdeig;           /* bisection + inverse iteration on the tridiagonal matrices */
   int64_t eig_tridiag;       /* Gram eigenproblems solved by the tridiagonal route */
   int64_t eig_fallbacks;     /* Gram eigenproblems handed to the iterative (Jacobi) eigensolver */
+  double ms_gemm_oz, flop_gemm_oz; /* tcgen05 GEMMs on exact bf16 slices (2MNK flops of the FP64 product) */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */
@@ -268,6 +278,14 @@ void fasttt_debug_fail_alloc_after(int64_t n);
  * Ogita-Aishima refinement + FP64 Jacobi polish only; 2: 0, else 1 (what the
  * library uses).  stream: cudaStream_t or NULL; returns after synchronising it. */
 int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_lam, int method, void* stream);
+
+/* Test hook for the GEMM engines (the paper has no counterpart): C = A B with
+ * A (M x K), B (K x N), C (M x N) row-major FP64 device arrays.  engine 0: FP64
+ * DFMA; 1: tcgen05 on 7 exact bf16 slices (FP64-level); 2: tcgen05 on 3 slices
+ * (FP32-level); 3: split-TF32 mma.sync (FP32-level).  FASTTT_ENUMERIC when the
+ * tensor-core kernel declined or gave up.  Synchronises the stream. */
+int fasttt_debug_gemm(int64_t M, int64_t N, int64_t K, const double* d_A, const double* d_B, double* d_C, int engine,
+                      void* stream);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,11 @@ int64_t launch_count();
 void note_block_sweep(int err);
 int64_t block_sweep_count();
 int last_coop_error();
-void note_eig(bool tridiag);   // Gram eigensolver: tridiagonal route taken, or the iterative fallback
+void note_eig(bool tridiag);
+// GEMM engine for the FP64 GEMMs of the calling thread: 0 = tensor cores (exact bf16
+// slices) for large products, 1 = FP64 DFMA only.
+void set_gemm_engine(int engine);
+int gemm_engine();   // Gram eigensolver: tridiagonal route taken, or the iterative fallback
 
 #define FTT_CUDA(call) ::fasttt::cuda_check((call), #call, __FILE__, __LINE__)
 #define FTT_LAUNCH()                                                             \
@@ -59,7 +63,8 @@ enum KernelClass {
   KC_GEMM_TC = 4,
   KC_TRIDIAG = 5,   // Householder tridiagonalisation
   KC_TDEIG = 6,     // bisection + inverse iteration on the tridiagonal matrix
-  KC_COUNT = 7
+  KC_GEMM_OZ = 7,   // tcgen05 GEMMs on exact bf16 slices of FP64 operands
+  KC_COUNT = 8
 };
 struct KClock {
   cudaEvent_t a = nullptr, b = nullptr;

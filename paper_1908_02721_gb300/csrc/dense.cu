@@ -899,11 +899,11 @@ int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& 
 void orthonormalise_cols_tc(double* U, int64_t rows, int64_t r, cudaStream_t s) {
   DBuf<double> S((size_t)r * r, s), U0((size_t)rows * r, s);
   for (int it = 0; it < 2; ++it) {
-    gemm_tf32x3(r, r, rows, 1.0, U, 1, r, U, r, 1, 0.0, S.get(), r, 1, s, true);   // U^T U
+    gemm(true, r, r, rows, 1.0, U, 1, r, U, r, 1, 0.0, S.get(), r, 1, s, true);   // U^T U
     i_minus_kernel<<<grid_for(r * r), 256, 0, s>>>(S.get(), r);
     FTT_LAUNCH();
     FTT_CUDA(cudaMemcpyAsync(U0.get(), U, sizeof(double) * rows * r, cudaMemcpyDeviceToDevice, s));
-    gemm_tf32x3(rows, r, r, 0.5, U0.get(), r, 1, S.get(), r, 1, 1.0, U, r, 1, s);
+    gemm(true, rows, r, r, 0.5, U0.get(), r, 1, S.get(), r, 1, 1.0, U, r, 1, s);
   }
 }
 
@@ -962,6 +962,15 @@ int64_t sym_eig_mixed32(const double* G, int n, double* V, std::vector<double>& 
 void gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
               const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
               cudaStream_t s, bool sym) {
+  if (gemm_engine() == 0 && K >= 64 && (double)M * (double)N * (double)K >= kTensorGemmMin &&
+      gemm_ozaki(7, M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym))
+    return;
+  gemm_f64_dfma(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+}
+
+void gemm_f64_dfma(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
+                   const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
+                   cudaStream_t s, bool sym) {
   if (M <= 0 || N <= 0) return;
   if (sym && (M != N || sci != N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
   const int64_t gx = ceil_div(M, kTile), gy = ceil_div(N, kTile);

@@ -8,13 +8,31 @@
 
 namespace fasttt {
 
-// C(i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j) with element strides.
-// sym = true: C is known to be symmetric (square, row-major); only tiles on or
-// above the diagonal are computed and the lower triangle is mirrored.
-// A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj], C(i,j) = C[i*sci + j*scj].
+// C(i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j) with element strides, to
+// FP64 accuracy.  sym = true: C is known to be symmetric (square, row-major);
+// only tiles on or above the diagonal are computed and the lower triangle is
+// mirrored.  A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj],
+// C(i,j) = C[i*sci + j*scj].  Large products run on the tensor cores (exact bf16
+// slices, gemm_ozaki with 7 slices) unless the engine is set to DFMA; the rest,
+// and any product the tensor path declines, on gemm_f64_dfma.
 void gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
               const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
               cudaStream_t s, bool sym = false);
+
+// The same product with FP64 DFMA (64 x 64 x 16 shared-memory tiles).
+void gemm_f64_dfma(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
+                   const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
+                   cudaStream_t s, bool sym = false);
+
+// The product on the tcgen05 tensor cores from exact bf16 slices of the operands
+// (gemm_ozaki.cu): slices = 7 gives FP64-level products, 3 FP32-level.  Returns
+// false (C untouched) when it does not apply or its kernel gave up.
+bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai,
+                int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci,
+                int64_t scj, cudaStream_t s, bool sym = false);
+
+// Products below this many multiply-adds stay on the DFMA / mma.sync kernels.
+constexpr double kTensorGemmMin = 67108864.0;   // 2^26
 
 // The same product as gemm_f64 on the tensor cores: split-TF32 operands (3
 // products), FP32 accumulation, FP64 in and out.  FP32-level accuracy.
@@ -22,12 +40,19 @@ void gemm_tf32x3(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                  const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
                  cudaStream_t s, bool sym = false);
 
-// gemm_f64 or, with mixed = true, gemm_tf32x3.
+// gemm_f64 or, with mixed = true, an FP32-level product: the tcgen05 kernel on 3
+// exact bf16 slices for large products, split-TF32 mma.sync otherwise.
 inline void gemm(bool mixed, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai,
                  int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci,
                  int64_t scj, cudaStream_t s, bool sym = false) {
-  if (mixed) gemm_tf32x3(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
-  else gemm_f64(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  if (!mixed) {
+    gemm_f64(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+    return;
+  }
+  if (gemm_engine() == 0 && (double)M * (double)N * (double)K >= kTensorGemmMin &&
+      gemm_ozaki(3, M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym))
+    return;
+  gemm_tf32x3(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
 }
 
 // dst (cols x rows, row-major) = transpose of src (rows x cols, row-major)

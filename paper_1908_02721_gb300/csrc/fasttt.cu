@@ -62,6 +62,11 @@ std::atomic<int64_t> g_block_sweeps{0};
 std::atomic<int> g_coop_err{0};
 std::atomic<int64_t> g_eig_tridiag{0}, g_eig_fallback{0};
 }  // namespace
+namespace {
+thread_local int g_gemm_engine = 0;
+}
+void set_gemm_engine(int engine) { g_gemm_engine = engine; }
+int gemm_engine() { return g_gemm_engine; }
 void note_eig(bool tridiag) { (tridiag ? g_eig_tridiag : g_eig_fallback).fetch_add(1, std::memory_order_relaxed); }
 void note_block_sweep(int err) {
   if (err) g_coop_err.store(err);
@@ -285,6 +290,8 @@ void finish_stats(fasttt_stats& st, int64_t launches0) {
   st.ms_tridiag = ms[KC_TRIDIAG];
   st.flop_tridiag = work[KC_TRIDIAG];
   st.ms_tdeig = ms[KC_TDEIG];
+  st.ms_gemm_oz = ms[KC_GEMM_OZ];
+  st.flop_gemm_oz = work[KC_GEMM_OZ];
   kclock_reset();
   st.launches = launch_count() - launches0;
 }
@@ -313,8 +320,11 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   if (o.precision != FASTTT_PREC_FP64 && o.precision != FASTTT_PREC_MIXED) fail(FASTTT_EINVAL, "unsupported precision");
   const bool mixed = (o.precision == FASTTT_PREC_MIXED);
   if (o.stage != FASTTT_STAGE_FULL && o.stage != FASTTT_STAGE_EXACT) fail(FASTTT_EINVAL, "bad stage");
-  if (o.sparse_sweep < FASTTT_SWEEP_AUTO || o.sparse_sweep > FASTTT_SWEEP_DENSE || o.reserved != 0)
+  if (o.sparse_sweep < FASTTT_SWEEP_AUTO || o.sparse_sweep > FASTTT_SWEEP_DENSE)
     fail(FASTTT_EINVAL, "bad sparse_sweep mode");
+  if (o.gemm_engine != FASTTT_GEMM_TENSOR && o.gemm_engine != FASTTT_GEMM_DFMA)
+    fail(FASTTT_EINVAL, "bad gemm_engine");
+  set_gemm_engine(o.gemm_engine);
   const int64_t max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
   fasttt_stats& st = H.st;
   st.d = d;
@@ -785,6 +795,23 @@ const char* fasttt_version(void) { return "fasttt-gb300 0.1 (sm_103a)"; }
 void fasttt_debug_fail_alloc_after(int64_t n) {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
   g_fail_after = n > 0 ? n : 0;
+}
+
+int fasttt_debug_gemm(int64_t M, int64_t N, int64_t K, const double* d_A, const double* d_B, double* d_C, int engine,
+                      void* stream) {
+  try {
+    if (M < 1 || N < 1 || K < 1 || !d_A || !d_B || !d_C || engine < 0 || engine > 3)
+      fail(FASTTT_EINVAL, "fasttt_debug_gemm: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (engine == 0) gemm_f64_dfma(M, N, K, 1.0, d_A, K, 1, d_B, N, 1, 0.0, d_C, N, 1, s);
+    else if (engine == 3) gemm_tf32x3(M, N, K, 1.0, d_A, K, 1, d_B, N, 1, 0.0, d_C, N, 1, s);
+    else if (!gemm_ozaki(engine == 1 ? 7 : 3, M, N, K, 1.0, d_A, K, 1, d_B, N, 1, 0.0, d_C, N, 1, s))
+      fail(FASTTT_ENUMERIC, "tensor-core GEMM declined or gave up");
+    FTT_CUDA(cudaStreamSynchronize(s));
+    return FASTTT_OK;
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
 }
 
 int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_lam, int method, void* stream) {

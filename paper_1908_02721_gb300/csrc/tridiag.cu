@@ -31,6 +31,8 @@ namespace {
 
 constexpr int kWYBlock = 64;
 
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
 __global__ void __launch_bounds__(256)
     tridiag_kernel(double* A, int64_t n, double* d, double* e, double* tau, double* p, unsigned* bar) {
   extern __shared__ double vs[];   // the current reflector v (v_0 = 1)
@@ -219,6 +221,42 @@ __global__ void wy_vectors_kernel(const double* A, int64_t n, int64_t k0, int64_
   }
 }
 
+// S += V^T V for the rows of V (nr x kb row-major, kb <= 64) in this block's
+// slice of rows (split over the grid; partial sums added by FP64 atomics).
+__global__ void __launch_bounds__(256) wy_gram_kernel(const double* __restrict__ V, int64_t nr, int64_t kb,
+                                                      double* __restrict__ S) {
+  __shared__ double tile[16][64 + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  const int64_t per = ceil_div_dev(nr, gridDim.x);
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(nr, r0 + per);
+  for (int64_t k0 = r0; k0 < r1; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int kk = e >> 6, c = e & 63;
+      tile[kk][c] = (k0 + kk < r1 && c < kb) ? V[(k0 + kk) * kb + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = tile[kk][ty + 16 * q]; b[q] = tile[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[q][w] = fma(a[q], b[w], acc[q][w]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = ty + 16 * q, j = tx + 16 * w;
+      if (i < kb && j < kb) atomicAdd(S + i * kb + j, acc[q][w]);
+    }
+}
+
 // T (kb x kb, upper triangular, row-major) of H_1 ... H_kb = I - V T V^T from
 // S = V^T V and the tau: T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] S[0:i, i].
 __global__ void wy_t_kernel(const double* S, const double* tau, int64_t kb, double* T) {
@@ -381,7 +419,10 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
       const int64_t kb = std::min<int64_t>(kWYBlock, nrefl - k0), nr = n - k0 - 1;
       wy_vectors_kernel<<<grid_for(nr * kb), 256, 0, s>>>(A.get(), n, k0, kb, Vb.get());
       FTT_LAUNCH();
-      gemm_f64(kb, kb, nr, 1.0, Vb.get(), 1, kb, Vb.get(), kb, 1, 0.0, S.get(), kb, 1, s);
+      FTT_CUDA(cudaMemsetAsync(S.get(), 0, sizeof(double) * kb * kb, s));
+      wy_gram_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nr, 64), kNumSMs)), 256, 0, s>>>(
+          Vb.get(), nr, kb, S.get());
+      FTT_LAUNCH();
       wy_t_kernel<<<1, 64, 0, s>>>(S.get(), tau.get() + k0, kb, T.get());
       FTT_LAUNCH();
       double* Zs = Z.get() + (k0 + 1) * n;

@@ -27,6 +27,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 STATIC, DYNAMIC = 0, 1
 STAGE_FULL, STAGE_EXACT = 0, 1
 SWEEP_MODES = {"auto": 0, "sparse": 1, "dense": 2}
+GEMM_ENGINES = {"tensor": 0, "dfma": 1}
 ARR = {name: i for i, name in enumerate([
     "core", "left_parent", "left_index", "right_index", "right_child", "mid_row", "mid_col", "mid_val",
     "row_id", "row_class", "row_pref", "col_id", "col_class", "col_pref", "dp_row", "dp_col", "dp_val",
@@ -44,7 +45,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("rounding", ctypes.c_int),
                 ("depar_values", ctypes.c_int), ("stage", ctypes.c_int), ("keep_intermediates", ctypes.c_int),
                 ("max_rank", ctypes.c_int64), ("max_sweeps", ctypes.c_int64), ("sparse_sweep", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("gemm_engine", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -63,7 +64,8 @@ class Stats(ctypes.Structure):
                 ("flop_jacobi32", ctypes.c_double), ("ms_gemm_tc", ctypes.c_double),
                 ("flop_gemm_tc", ctypes.c_double), ("sparse_bonds", ctypes.c_int64),
                 ("ms_tridiag", ctypes.c_double), ("flop_tridiag", ctypes.c_double), ("ms_tdeig", ctypes.c_double),
-                ("eig_tridiag", ctypes.c_int64), ("eig_fallbacks", ctypes.c_int64)]
+                ("eig_tridiag", ctypes.c_int64), ("eig_fallbacks", ctypes.c_int64),
+                ("ms_gemm_oz", ctypes.c_double), ("flop_gemm_oz", ctypes.c_double)]
 
     def to_dict(self):
         d = self.d
@@ -82,7 +84,8 @@ class Stats(ctypes.Structure):
                 "ms_gemm_tc": self.ms_gemm_tc, "flop_gemm_tc": self.flop_gemm_tc,
                 "sparse_bonds": self.sparse_bonds, "ms_tridiag": self.ms_tridiag,
                 "flop_tridiag": self.flop_tridiag, "ms_tdeig": self.ms_tdeig, "eig_tridiag": self.eig_tridiag,
-                "eig_fallbacks": self.eig_fallbacks}
+                "eig_fallbacks": self.eig_fallbacks, "ms_gemm_oz": self.ms_gemm_oz,
+                "flop_gemm_oz": self.flop_gemm_oz}
 
 
 _P = ctypes.c_void_p
@@ -107,11 +110,13 @@ _lib.fasttt_last_error.restype = ctypes.c_char_p
 _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
 _lib.fasttt_debug_sym_eig.argtypes = [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, _P]
+_lib.fasttt_debug_gemm.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _P]
 
 EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_tt_stats", "fasttt_tt_ranks",
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
            "tt_eval_backward_noalloc",
-           "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig"]
+           "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig",
+           "fasttt_debug_gemm"]
 
 
 class FastTTError(RuntimeError):
@@ -152,6 +157,25 @@ def debug_sym_eig(G, method="auto", stream=None):
                                    _stream(stream))
     _check(rc)
     return lam, V
+
+
+GEMM_TEST_ENGINES = {"dfma": 0, "tensor_f64": 1, "tensor_f32": 2, "tf32x3": 3}
+
+
+def debug_gemm(A, B, engine, stream=None):
+    """C = A @ B for FP64 CUDA matrices through one of the library's GEMM kernels (a test hook)."""
+    _require_cuda()
+    A = _dev(A, torch.float64)
+    B = _dev(B, torch.float64)
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K:
+        raise FastTTError(EINVAL, "inner dimensions differ")
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    rc = _lib.fasttt_debug_gemm(M, N, K, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                ctypes.c_void_p(C.data_ptr()), GEMM_TEST_ENGINES[engine], _stream(stream))
+    _check(rc)
+    return C
 
 
 def _require_cuda():
@@ -224,10 +248,12 @@ class TT:
 
 def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True, rounding="static",
                      stage="full", keep_intermediates=False, max_sweeps=0, precision="fp64", sparse_sweep="auto",
-                     stream=None) -> TT:
+                     gemm_engine="tensor", stream=None) -> TT:
     """FastTT (Alg. 7) of the COO tensor (idx (d, nnz) int32, vals float64/float32).
 
-    sparse_sweep: "auto", "sparse" or "dense", how the first SVD sweep holds its cores."""
+    sparse_sweep: "auto", "sparse" or "dense", how the first SVD sweep holds its cores.
+    gemm_engine: "tensor" (large FP64 products on the tensor cores from exact bf16 slices)
+    or "dfma" (FP64 DFMA only)."""
     _require_cuda()
     idx = _dev(idx, torch.int32)
     if isinstance(vals, np.ndarray):
@@ -250,6 +276,9 @@ def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True
     if sparse_sweep not in SWEEP_MODES:
         raise FastTTError(EINVAL, "sparse_sweep must be 'auto', 'sparse' or 'dense'")
     o.sparse_sweep = SWEEP_MODES[sparse_sweep]
+    if gemm_engine not in GEMM_ENGINES:
+        raise FastTTError(EINVAL, "gemm_engine must be 'tensor' or 'dfma'")
+    o.gemm_engine = GEMM_ENGINES[gemm_engine]
     out = ctypes.c_void_p(0)
     st = Stats()
     rc = _lib.fasttt_decompose(d, _i64arr(dims), int(idx.shape[1]), ctypes.c_void_p(idx.data_ptr()),

@@ -43,12 +43,35 @@ def test_binding_loads_and_matches_exports(lib):
     assert o.p == 0 and o.depar_values == 1 and o.max_rank == 0
 
 
+def _struct_fields(name):
+    """Field names of `typedef struct name {...} name;` in the header, in order."""
+    txt = open(os.path.join(ROOT, "include", "fasttt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), txt, flags=re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"\[[^\]]*\]", "", decl)
+        first, *rest = [d.strip() for d in decl.split(",")]
+        out.append(first.split()[-1])
+        out.extend(rest)
+    return out
+
+
+def test_struct_field_order_matches_header(lib):
+    from paper_1908_02721_gb300 import fasttt as F
+    assert [f[0] for f in F.Opts._fields_] == _struct_fields("fasttt_opts")
+    assert [f[0] for f in F.Stats._fields_] == _struct_fields("fasttt_stats")
+
+
 def test_struct_layouts_match_header(lib):
     from paper_1908_02721_gb300 import fasttt as F
     # fasttt_opts: six ints, two int64, two ints; fasttt_stats ends with the kernel-class doubles
     assert ctypes.sizeof(F.Opts) == 8 * 4 + 2 * 8
     assert F.Opts.sparse_sweep.offset == 6 * 4 + 2 * 8
-    assert F.Stats.eig_fallbacks.offset + 8 == ctypes.sizeof(F.Stats)
+    assert F.Stats.flop_gemm_oz.offset + 8 == ctypes.sizeof(F.Stats)
 
 
 def test_calls_without_gpu_fail_loudly(lib):
