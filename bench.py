@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FastTT nnz/s at rel. err <=1e-6 (FP64 vs mixed, 1 GB300); adjoint % HBM roofline"
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
 SAMPLE_N = 30                                       # oracle sample: same recipe at mode size 30
+OZ_PAIRS_FP64 = 28                                  # slice pairs (s, t), s + t <= 8, of the 7-slice product
 
 
 def _peaks():
@@ -211,15 +212,23 @@ def run_ours(args):
         return
     st = stats[-1]
     peaks, src = _peaks()
-    # dominant kernel class by device time
-    classes = {"gemm_f64": (st["ms_gemm"], st["flop_gemm"]), "jacobi_f64": (st["ms_jacobi"], st["flop_jacobi"]),
-               "tridiag_f64": (st["ms_tridiag"], st["flop_tridiag"])}
-    name, (kms, kwork) = max(classes.items(), key=lambda kv: kv[1][0])
+    # dominant kernel class by device time.  The tcgen05 GEMM computes an FP64 product from 7
+    # exact bf16 slices per operand: 28 slice-pair products, so its tensor-pipe work is
+    # 28 x 2MNK bf16 flops, measured against the bf16 dense peak.
+    bf16_peak = peaks.get("bf16_tflops", 1921.5)
+    classes = {"gemm_f64_kernel": (st["ms_gemm"], st["flop_gemm"], "alu", FP64_PEAK_TFLOPS),
+               "jacobi_sweep_kernel<double>": (st["ms_jacobi"], st["flop_jacobi"], "alu", FP64_PEAK_TFLOPS),
+               "tridiag_kernel": (st["ms_tridiag"], st["flop_tridiag"], "alu", FP64_PEAK_TFLOPS),
+               "ozaki_gemm_kernel<7>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor", bf16_peak)}
+    name, (kms, kwork, bound, peak) = max(classes.items(), key=lambda kv: kv[1][0])
     achieved = kwork / (kms / 1e3) / 1e12 if kms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 DFMA: 2 per clock per SM x 152 SMs x 2070 MHz (derived; measured 1.198)",
+    roofline = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": ("bf16 dense, measured (MEASURED_PEAKS.json bf16_tflops burst)" if bound == "tensor" else
+                                "FP64 DFMA: 2 per clock per SM x 152 SMs x 2070 MHz (derived; measured 1.198)"),
                 "share_of_step": kms / st["ms_total"] if st["ms_total"] else None}
+    if st["ms_gemm_oz"] > 0:
+        roofline["ozaki_fp64_equivalent_tflops"] = st["flop_gemm_oz"] / (st["ms_gemm_oz"] / 1e3) / 1e12
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sw = _sample_workload()
@@ -241,7 +250,7 @@ def run_ours(args):
             "adjoint": adjoint_line,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
-            "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm",
+            "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm_oz", "ms_gemm",
                                               "ms_jacobi", "ms_tridiag", "ms_tdeig", "ms_jacobi32", "ms_sort")},
             "gram_eigensolver": {"tridiagonal": st["eig_tridiag"], "iterative_fallback": st["eig_fallbacks"]},
             "jacobi_sweeps": st["jacobi_sweeps"],
@@ -289,10 +298,10 @@ def _mixed(args, F, idx, vals, w, flush, stream):
     tt.free()
     tc = st["ms_gemm_tc"]
     return {"value": w.nnz / (ms / 1e3), "unit": "nnz/s", "ms_per_step": ms, "rel_err_sampled": err,
-            "ranks": st["ranks"], "dtype": "tf32x3 tensor-core contractions + f32/f64",
+            "ranks": st["ranks"], "dtype": "bf16-slice (3 slices) tensor-core contractions + f32/f64",
             "tensor_gemm": {"ms": tc, "tflops": st["flop_gemm_tc"] / (tc / 1e3) / 1e12 if tc else None},
-            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_tc", "ms_gemm", "ms_jacobi", "ms_tridiag",
-                                              "ms_tdeig", "ms_jacobi32")}}
+            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_oz", "ms_gemm_tc", "ms_gemm", "ms_jacobi",
+                                              "ms_tridiag", "ms_tdeig", "ms_jacobi32")}}
 
 
 def _adjoint(args, F, dev, stream):
