@@ -29,8 +29,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FastTT nnz/s at rel. err <=1e-6 (FP64 vs mixed, 1 GB300); adjoint % HBM roofline"
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
+FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12  # 128 FFMA/clk/SM x 152 SMs x 2070 MHz
 SAMPLE_N = 30                                       # oracle sample: same recipe at mode size 30
-OZ_PAIRS_FP64 = 28                                  # slice pairs (s, t), s + t <= 8, of the 7-slice product
+OZ_PAIRS_FP64 = 36                                  # slice pairs (s, t), s + t <= 9, of the 8-slice product
 
 
 def _peaks():
@@ -212,19 +213,22 @@ def run_ours(args):
         return
     st = stats[-1]
     peaks, src = _peaks()
-    # dominant kernel class by device time.  The tcgen05 GEMM computes an FP64 product from 7
-    # exact bf16 slices per operand: 28 slice-pair products, so its tensor-pipe work is
-    # 28 x 2MNK bf16 flops, measured against the bf16 dense peak.
+    # dominant kernel class by device time.  The tcgen05 GEMM computes an FP64 product from 8
+    # exact bf16 slices per operand: 36 slice-pair products, so its tensor-pipe work is
+    # 36 x 2MNK bf16 flops, measured against the bf16 dense peak.
     bf16_peak = peaks.get("bf16_tflops", 1921.5)
     classes = {"gemm_f64_kernel": (st["ms_gemm"], st["flop_gemm"], "alu", FP64_PEAK_TFLOPS),
                "jacobi_sweep_kernel<double>": (st["ms_jacobi"], st["flop_jacobi"], "alu", FP64_PEAK_TFLOPS),
                "tridiag_kernel": (st["ms_tridiag"], st["flop_tridiag"], "alu", FP64_PEAK_TFLOPS),
-               "ozaki_gemm_kernel<7>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor", bf16_peak)}
+               "ozaki_gemm_kernel<8,7,256>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor", bf16_peak),
+               "tridiag_kernel<float>": (st["ms_tridiag32"], st["flop_tridiag32"], "alu", FP32_PEAK_TFLOPS),
+               "qr_blocks_kernel+qr_apply_kernel": (st["ms_tsqr"], st["flop_tsqr"], "alu", FP64_PEAK_TFLOPS)}
     name, (kms, kwork, bound, peak) = max(classes.items(), key=lambda kv: kv[1][0])
     achieved = kwork / (kms / 1e3) / 1e12 if kms > 0 else 0.0
     roofline = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": ("bf16 dense, measured (MEASURED_PEAKS.json bf16_tflops burst)" if bound == "tensor" else
+                                "FP32 FFMA: 128 per clock per SM x 152 SMs x 2070 MHz (derived)" if peak == FP32_PEAK_TFLOPS else
                                 "FP64 DFMA: 2 per clock per SM x 152 SMs x 2070 MHz (derived; measured 1.198)"),
                 "share_of_step": kms / st["ms_total"] if st["ms_total"] else None}
     if st["ms_gemm_oz"] > 0:
@@ -251,8 +255,10 @@ def run_ours(args):
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm_oz", "ms_gemm",
-                                              "ms_jacobi", "ms_tridiag", "ms_tdeig", "ms_jacobi32", "ms_sort")},
-            "gram_eigensolver": {"tridiagonal": st["eig_tridiag"], "iterative_fallback": st["eig_fallbacks"]},
+                                              "ms_jacobi", "ms_tsqr", "ms_tridiag32", "ms_tridiag", "ms_tdeig",
+                                              "ms_jacobi32", "ms_sort")},
+            "gram_eigensolver": {"fast": st["eig_fast"], "tridiagonal": st["eig_tridiag"],
+                                 "iterative_fallback": st["eig_fallbacks"]},
             "jacobi_sweeps": st["jacobi_sweeps"],
             "wall_s": wall, "peaks_source": src}
     print(json.dumps(line), flush=True)
@@ -300,8 +306,8 @@ def _mixed(args, F, idx, vals, w, flush, stream):
     return {"value": w.nnz / (ms / 1e3), "unit": "nnz/s", "ms_per_step": ms, "rel_err_sampled": err,
             "ranks": st["ranks"], "dtype": "bf16-slice (3 slices) tensor-core contractions + f32/f64",
             "tensor_gemm": {"ms": tc, "tflops": st["flop_gemm_tc"] / (tc / 1e3) / 1e12 if tc else None},
-            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_oz", "ms_gemm_tc", "ms_gemm", "ms_jacobi",
-                                              "ms_tridiag", "ms_tdeig", "ms_jacobi32")}}
+            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_oz", "ms_gemm_tc", "ms_gemm", "ms_jacobi", "ms_tsqr",
+                                              "ms_tridiag32", "ms_tridiag", "ms_tdeig", "ms_jacobi32")}}
 
 
 def _adjoint(args, F, dev, stream):

@@ -81,10 +81,12 @@ typedef struct fasttt_opts {
 
 /* Engine of the dense FP64 contractions.  TENSOR: products of at least 2^26
  * multiply-adds run on the tcgen05 tensor cores from exact bf16 slices of the
- * FP64 operands (7 slices: every slice product exact, FP64 accumulation of the
- * exact FP32 partial sums; FP64-level results, Ozaki-Ogita-Oishi-Rump splitting),
- * smaller ones on FP64 DFMA.  DFMA: every FP64 product on FP64 DFMA.  In mixed
- * precision, TENSOR runs the large products from 3 slices (FP32-level). */
+ * FP64 operands (8 slices of 7 bits: every slice product exact, the level sums
+ * exact in FP32 over windows of 256 and then in 64-bit integers; FP64-level
+ * results, Ozaki-Ogita-Oishi-Rump splitting), smaller ones on FP64 DFMA.  DFMA:
+ * every FP64 product on FP64 DFMA.  In mixed precision, TENSOR runs the large
+ * products from 3 slices of 8 bits (FP32-level).  A tensor-core kernel whose
+ * bounded wait gives up makes the call fail with FASTTT_ETIMEOUT. */
 #define FASTTT_GEMM_TENSOR 0
 #define FASTTT_GEMM_DFMA 1
 
@@ -131,9 +133,12 @@ typedef struct fasttt_stats {
   int64_t sparse_bonds;      /* first-sweep bonds run block-sparse (FASTTT_SWEEP_SPARSE path) */
   double ms_tridiag, flop_tridiag; /* Householder tridiagonalisation of Gram matrices (2 n^3 flops) */
   double ms_tdeig;           /* bisection + inverse iteration on the tridiagonal matrices */
-  int64_t eig_tridiag;       /* Gram eigenproblems solved by the tridiagonal route */
+  int64_t eig_tridiag;       /* Gram eigenproblems solved by the FP64 tridiagonal route */
   int64_t eig_fallbacks;     /* Gram eigenproblems handed to the iterative (Jacobi) eigensolver */
   double ms_gemm_oz, flop_gemm_oz; /* tcgen05 GEMMs on exact bf16 slices (2MNK flops of the FP64 product) */
+  double ms_tridiag32, flop_tridiag32; /* FP32 tridiagonalisation of the fast eigensolver's start (2 n^3 flops) */
+  double ms_tsqr, flop_tsqr;  /* Householder TSQR of tall-skinny SVDs and its Q application (4 m n^2 flops each) */
+  int64_t eig_fast;           /* Gram eigenproblems solved by the fast route (FP32 start + refinement) */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */
@@ -273,10 +278,13 @@ void fasttt_debug_fail_alloc_after(int64_t n);
  * be checked on matrices with chosen spectra).  d_G: symmetric n x n FP64,
  * row-major, device, read only.  d_V: n x n device output, eigenvector j in
  * d_V[j*n .. j*n + n).  h_lam: n host doubles, eigenvalue j (unordered).
- * method 0: Householder tridiagonalisation + bisection + inverse iteration
- * only (FASTTT_ENUMERIC when that route declines); 1: FP32 Jacobi start +
- * Ogita-Aishima refinement + FP64 Jacobi polish only; 2: 0, else 1 (what the
- * library uses).  stream: cudaStream_t or NULL; returns after synchronising it. */
+ * method 0: FP64 Householder tridiagonalisation + bisection + inverse
+ * iteration only (FASTTT_ENUMERIC when that route declines); 1: FP32 Jacobi
+ * start + Ogita-Aishima refinement + FP64 Jacobi polish only; 2: 3, else 0,
+ * else 1 (what the library uses); 3: the fast route only (FP32 tridiagonal
+ * start, Ogita-Aishima refinement with FP64-level tensor-core products,
+ * Rayleigh-Ritz on runs of close eigenvalues; FASTTT_ENUMERIC when it
+ * declines).  stream: cudaStream_t or NULL; returns after synchronising it. */
 int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_lam, int method, void* stream);
 
 /* Test hook for the GEMM engines (the paper has no counterpart): C = A B with
@@ -286,6 +294,27 @@ int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_la
  * tensor-core kernel declined or gave up.  Synchronises the stream. */
 int fasttt_debug_gemm(int64_t M, int64_t N, int64_t K, const double* d_A, const double* d_B, double* d_C, int engine,
                       void* stream);
+
+/* Test hook for the dense SVD of the rounding sweeps (the paper has no
+ * counterpart; it exposes the SVD behind S7-S10 so that it can be checked on
+ * matrices with chosen singular values).  d_Z: M x N FP64, row-major, device,
+ * read only.  All min(M, N) singular values are kept: h_sigma receives them
+ * (host, descending), d_U (M x r row-major) and d_Vt (r x N row-major, device,
+ * caller-allocated, r = min(M, N)) the factors with Z = U diag(sigma) Vt.
+ * precision: FASTTT_PREC_FP64 or FASTTT_PREC_MIXED.  The route is the library's
+ * (one-sided Jacobi, through TSQR for tall-skinny shapes, or the Gram route).
+ * FASTTT_EINVAL for bad arguments.  Synchronises the stream. */
+int fasttt_debug_svd(int64_t M, int64_t N, const double* d_Z, double* h_sigma, double* d_U, double* d_Vt,
+                     int precision, void* stream);
+
+/* Test hook for the symmetric (Gram) products of the rounding stage: C = A A^T
+ * (M x M, row-major) for a row-major M x K device matrix A, through the same
+ * engines as fasttt_debug_gemm (0..3) on their symmetric path: only the tiles
+ * on or above the diagonal are computed and mirrored, and the tensor-core
+ * engines split A once for both operands.  Caller-owned device buffers;
+ * FASTTT_EINVAL for bad arguments, FASTTT_ENUMERIC when a tensor-core kernel
+ * declined or gave up.  Synchronises the stream. */
+int fasttt_debug_gram(int64_t M, int64_t K, const double* d_A, double* d_C, int engine, void* stream);
 
 #ifdef __cplusplus
 }

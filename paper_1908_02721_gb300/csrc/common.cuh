@@ -41,6 +41,7 @@ void note_block_sweep(int err);
 int64_t block_sweep_count();
 int last_coop_error();
 void note_eig(bool tridiag);
+void note_eig_fast();
 // GEMM engine for the FP64 GEMMs of the calling thread: 0 = tensor cores (exact bf16
 // slices) for large products, 1 = FP64 DFMA only.
 void set_gemm_engine(int engine);
@@ -64,7 +65,9 @@ enum KernelClass {
   KC_TRIDIAG = 5,   // Householder tridiagonalisation
   KC_TDEIG = 6,     // bisection + inverse iteration on the tridiagonal matrix
   KC_GEMM_OZ = 7,   // tcgen05 GEMMs on exact bf16 slices of FP64 operands
-  KC_COUNT = 8
+  KC_TRIDIAG32 = 8, // FP32 tridiagonalisation (fast eigensolver start)
+  KC_TSQR = 9,      // Householder TSQR and its Q application
+  KC_COUNT = 10
 };
 struct KClock {
   cudaEvent_t a = nullptr, b = nullptr;

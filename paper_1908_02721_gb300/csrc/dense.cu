@@ -758,13 +758,53 @@ __global__ void oa_lambda_kernel(const double* S, const double* R, int64_t n, do
 
 // The correction of the refinement step: e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)
 // for |lambda_j - lambda_i| > delta, e_ij = r_ij / 2 otherwise (clusters, diagonal).
+// guard > 0: the first-order correction is also withheld (e_ij = r_ij / 2) where it
+// would exceed guard in magnitude, i.e. where the pair is still mixed by more than
+// the first-order analysis covers (such pairs are left to the Rayleigh-Ritz step).
 __global__ void oa_correction_kernel(const double* S, const double* R, const double* lam, double delta, int64_t n,
-                                     double* E) {
+                                     double* E, double guard = 0.0) {
   GRID_STRIDE(e, n * n) {
     const int64_t i = e / n, j = e % n;
     const double d = lam[j] - lam[i];
-    E[e] = (i != j && fabs(d) > delta) ? (S[e] + lam[j] * R[e]) / d : 0.5 * R[e];
+    const double num = S[e] + lam[j] * R[e];
+    const bool first_order = (i != j && fabs(d) > delta && (guard == 0.0 || fabs(num) <= guard * fabs(d)));
+    E[e] = first_order ? num / d : 0.5 * R[e];
   }
+}
+
+// res[i] = sqrt(sum_{j != i} s_ij^2): the residual ||G x_i - lambda_i x_i|| of an
+// orthonormal X (one warp per row)
+__global__ void offdiag_row_norms_kernel(const double* S, int64_t n, double* res) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32)
+    if (j != row) acc = fma(S[row * n + j], S[row * n + j], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) res[row] = sqrt(acc);
+}
+
+// v <- y / ||y|| and est = ||y|| (one block; the power method's normalisation on the device)
+__global__ void __launch_bounds__(256) normalise_vec_kernel(const double* y, int64_t n, double* v, double* est) {
+  __shared__ double red[8];
+  __shared__ double nrm;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc = fma(y[i], y[i], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    nrm = sqrt(t);
+    *est = nrm;
+  }
+  __syncthreads();
+  const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v[i] = y[i] * inv;
 }
 
 // ||M - diag(d)||_2 of a symmetric n x n matrix by 12 steps of the power method
@@ -772,23 +812,20 @@ __global__ void oa_correction_kernel(const double* S, const double* R, const dou
 double norm2_sym(const double* M, const double* d, int64_t n, cudaStream_t s) {
   std::vector<double> h(n);
   for (int64_t i = 0; i < n; ++i) h[i] = 1.0 + 0.5 * sin(0.7 * (double)i + 0.3);
-  DBuf<double> v(n, s), y(n, s);
+  double nrm = 0.0;
+  for (double x : h) nrm += x * x;
+  nrm = sqrt(nrm);
+  for (auto& x : h) x /= nrm;
+  DBuf<double> v(n, s), y(n, s), est(1, s);
   FTT_CUDA(cudaMemcpyAsync(v.get(), h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  double est = 0.0;
   for (int it = 0; it < 12; ++it) {
     matvec_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(M, d, v.get(), n, y.get());
     FTT_LAUNCH();
-    FTT_CUDA(cudaMemcpyAsync(h.data(), y.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    FTT_CUDA(cudaStreamSynchronize(s));
-    double nrm = 0.0;
-    for (double x : h) nrm += x * x;
-    nrm = sqrt(nrm);
-    if (!(nrm > 0.0)) return 0.0;
-    est = nrm;   // ||M v|| with ||v|| = 1 after the first step
-    for (auto& x : h) x /= nrm;
-    FTT_CUDA(cudaMemcpyAsync(v.get(), h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    normalise_vec_kernel<<<1, 256, 0, s>>>(y.get(), n, v.get(), est.get());   // ||M v|| with ||v|| = 1
+    FTT_LAUNCH();
   }
-  return est;
+  const double e = read_scalar(est.get(), s);
+  return std::isfinite(e) ? e : 0.0;
 }
 
 double sumsq(const double* M, const double* diag, int64_t n, cudaStream_t s) {
@@ -894,6 +931,156 @@ int64_t sym_eig_refined(const double* G, int n, double* V, std::vector<double>& 
   return sweeps;
 }
 
+// dst row j = src row perm[j] (n x n row-major)
+__global__ void permute_rows_kernel(const double* src, const int32_t* perm, int64_t n, double* dst) {
+  GRID_STRIDE(e, n * n) dst[e] = src[(int64_t)perm[e / n] * n + e % n];
+}
+
+// Ogita-Aishima refinement (see sym_eig_refined) of approximate eigenvectors V
+// (row j = x_j) of the symmetric G, with FP64-level products (mixed: FP32-level
+// products, stopped at FP32-level residuals).  Pairs closer than the refinement's
+// separation threshold delta are left mixed by it; each run of such eigenvalues
+// that is wider than the rounding level gets a Rayleigh-Ritz step: FP64 one-sided
+// Jacobi on G X_c with the rotations applied to X_c.  Returns false when the
+// refinement does not converge (the caller takes another route).
+bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps, cudaStream_t s,
+                bool mixed) {
+  const int64_t nn = (int64_t)n * n;
+  const double g2 = sumsq(G, nullptr, n, s);
+  const double gF = sqrt(g2);
+  lam_out.assign(n, 0.0);
+  if (g2 == 0.0) return true;   // the zero matrix: the start's V = I is exact
+  if (!std::isfinite(g2)) return false;
+  DBuf<double> R(nn, s), W(nn, s), S(nn, s), lam(n, s), Vbak(nn, s);
+  const double u = mixed ? 0x1p-24 : 0x1p-53;
+  const double tiny = 64.0 * (double)n * u;
+  constexpr double kGuard = 1.0 / 16.0;   // largest first-order correction applied
+  double best = INFINITY;
+  int since_best = 0;
+  bool have_bak = false;
+  // X^T X, S = X^T G X and the Rayleigh quotients for the current V; returns err
+  auto evaluate = [&](double& rF, double& offS) {
+    gemm(mixed, n, n, n, 1.0, V, n, 1, V, 1, n, 0.0, R.get(), n, 1, s, true);        // X^T X
+    i_minus_kernel<<<grid_for(nn), 256, 0, s>>>(R.get(), n);
+    FTT_LAUNCH();
+    gemm(mixed, n, n, n, 1.0, V, n, 1, G, n, 1, 0.0, W.get(), n, 1, s);              // W = X^T G
+    gemm(mixed, n, n, n, 1.0, V, n, 1, W.get(), 1, n, 0.0, S.get(), n, 1, s, true);  // S = X^T G X
+    oa_lambda_kernel<<<grid_for(n), 256, 0, s>>>(S.get(), R.get(), n, lam.get());
+    FTT_LAUNCH();
+    offS = sqrt(sumsq(S.get(), lam.get(), n, s));
+    rF = sqrt(sumsq(R.get(), nullptr, n, s));
+    FTT_CUDA(cudaMemcpyAsync(lam_out.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    return rF + offS / gF;
+  };
+  // Quadratic convergence is not monotone in err (a large first-order step leaves a
+  // second-order loss of orthogonality that the next step removes): iterate until
+  // converged or two steps without a new best, then continue from the best state.
+  double rF = 0.0, offS = 0.0;
+  for (int it = 0; it < 8; ++it) {
+    const double err = evaluate(rF, offS);
+    if (!std::isfinite(err)) return false;
+    if (rF <= tiny && offS <= tiny * gF) { best = err; since_best = 0; break; }   // converged
+    if (err < best) {
+      best = err;
+      since_best = 0;
+      FTT_CUDA(cudaMemcpyAsync(Vbak.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+      have_bak = true;
+    } else if (++since_best >= 2) {
+      break;
+    }
+    if (!(rF < 0.5) || it == 7) break;   // the state of the last evaluation is kept
+    double lmax = 0.0;
+    for (double x : lam_out) lmax = std::max(lmax, fabs(x));
+    const double s2 = std::min(offS, 2.0 * norm2_sym(S.get(), lam.get(), n, s));
+    const double r2 = std::min(rF, 2.0 * norm2_sym(R.get(), nullptr, n, s));
+    const double delta = 2.0 * (s2 + lmax * r2);
+    oa_correction_kernel<<<grid_for(nn), 256, 0, s>>>(S.get(), R.get(), lam.get(), delta, n, W.get(), kGuard);
+    FTT_LAUNCH();
+    // X <- X + X E, in X^T layout: X^T <- X^T + E^T X^T
+    FTT_CUDA(cudaMemcpyAsync(S.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    gemm(mixed, n, n, n, 1.0, W.get(), 1, n, S.get(), n, 1, 1.0, V, n, 1, s);
+  }
+  if (since_best > 0 || !(rF < 0.5)) {
+    if (!have_bak) return false;
+    FTT_CUDA(cudaMemcpyAsync(V, Vbak.get(), sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    evaluate(rF, offS);
+    if (!(rF < 0.5)) return false;
+  }
+  // Runs of close eigenvalues (ascending) whose residuals are not small against
+  // their gap: the eigenvector error is bounded by residual / gap, so neighbours
+  // with gap <= 16 max(residual) are resolved together by Rayleigh-Ritz.
+  std::vector<double> res(n);
+  {
+    offdiag_row_norms_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(S.get(), n, lam.get());
+    FTT_LAUNCH();
+    FTT_CUDA(cudaMemcpyAsync(res.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<int32_t> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return lam_out[a] < lam_out[b]; });
+  double lmax = 0.0;
+  for (double x : lam_out) lmax = std::max(lmax, fabs(x));
+  const double wtol = 4.0 * (double)n * u * lmax;
+  const double ltol = (double)n * u * lmax;   // Rayleigh quotients err by about residual^2 / gap
+  std::vector<std::pair<int, int>> runs;
+  int64_t rr_work = 0;
+  auto coupled = [&](int a, int b) {
+    const double gap = lam_out[b] - lam_out[a], r = std::max(res[a], res[b]);
+    return gap <= 16.0 * r || r * r > ltol * gap;
+  };
+  for (int i = 0; i < n;) {
+    int j = i + 1;
+    while (j < n && coupled(perm[j - 1], perm[j])) ++j;
+    if (j - i >= 2 && lam_out[perm[j - 1]] - lam_out[perm[i]] > wtol) {
+      runs.emplace_back(i, j);
+      rr_work += (int64_t)(j - i) * (j - i);
+    }
+    i = j;
+  }
+  if (!runs.empty()) {
+    if ((double)rr_work * (double)n > 4.0e11) return false;   // too much Jacobi work: another route
+    DBuf<int32_t> dperm(n, s);
+    FTT_CUDA(cudaMemcpyAsync(dperm.get(), perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    permute_rows_kernel<<<grid_for(nn), 256, 0, s>>>(V, dperm.get(), n, W.get());
+    FTT_LAUNCH();
+    FTT_CUDA(cudaMemcpyAsync(V, W.get(), sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> sorted(n);
+    for (int i = 0; i < n; ++i) sorted[i] = lam_out[perm[i]];
+    lam_out = sorted;
+    FTT_CUDA(cudaStreamSynchronize(s));   // perm is host memory read by the copy above
+    DBuf<double> norms(n, s);
+    for (const auto& rn : runs) {
+      const int64_t j0 = rn.first, c = rn.second - rn.first;
+      double* Vc = V + j0 * n;
+      double* Wc = W.get() + j0 * n;
+      gemm(mixed, c, n, n, 1.0, Vc, n, 1, G, n, 1, 0.0, Wc, n, 1, s);   // rows j0.. of X^T G: (G x_j)^T
+      jacobi_f64(Wc, n, n, (int)c, Vc, n, n, max_sweeps, s);
+      col_norms_kernel<double><<<(unsigned)c, 256, 0, s>>>(Wc, n, n, (int)c, norms.get());
+      FTT_LAUNCH();
+      std::vector<double> h(c);
+      FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * c, cudaMemcpyDeviceToHost, s));
+      FTT_CUDA(cudaStreamSynchronize(s));
+      // the columns of G X_c have norms |lambda|; the run's Rayleigh quotients give the sign
+      const double sgn = (lam_out[j0] + lam_out[j0 + c - 1] < 0.0) ? -1.0 : 1.0;
+      for (int64_t q = 0; q < c; ++q) lam_out[j0 + q] = sgn * h[q];
+    }
+  }
+  // Orthonormalise X to the rounding level of the products (Newton-Schulz).
+  for (int it = 0; it < 3; ++it) {
+    gemm(mixed, n, n, n, 1.0, V, n, 1, V, 1, n, 0.0, R.get(), n, 1, s, true);
+    i_minus_kernel<<<grid_for(nn), 256, 0, s>>>(R.get(), n);
+    FTT_LAUNCH();
+    const double rF = sqrt(sumsq(R.get(), nullptr, n, s));
+    if (!(rF < 0.5)) return false;
+    if (rF <= 16.0 * (double)n * u) break;
+    FTT_CUDA(cudaMemcpyAsync(S.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    gemm(mixed, n, n, n, 0.5, R.get(), n, 1, S.get(), n, 1, 1.0, V, n, 1, s);
+  }
+  return true;
+}
+
 // Orthonormalise the columns of the row-major rows x r matrix U on the tensor
 // cores: U <- U + 0.5 U (I - U^T U), twice (quadratic while ||I - U^T U|| < 1).
 void orthonormalise_cols_tc(double* U, int64_t rows, int64_t r, cudaStream_t s) {
@@ -958,6 +1145,11 @@ int64_t sym_eig_mixed32(const double* G, int n, double* V, std::vector<double>& 
 }
 
 }  // namespace
+
+int64_t jacobi_svd_f64(double* A, int64_t m, int64_t lda, int n, double* V, int64_t nv, int64_t ldv,
+                       int64_t max_sweeps, cudaStream_t s) {
+  return jacobi_f64(A, m, lda, n, V, nv, ldv, max_sweeps, s);
+}
 
 void gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
               const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
@@ -1029,15 +1221,17 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
   if (direct) {
     identity_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(V.get(), n);
     FTT_LAUNCH();
-    out.sweeps = jacobi_f64(A.get(), m_len, lda, n, V.get(), n, n, max_sweeps, s);
+    if (tsqr_applies(m_len, n) && lda == m_len) out.sweeps = tsqr_jacobi(A.get(), m_len, n, V.get(), max_sweeps, s);
+    else out.sweeps = jacobi_f64(A.get(), m_len, lda, n, V.get(), n, n, max_sweeps, s);
     DBuf<double> norms(n, s);
     col_norms_kernel<double><<<n, 256, 0, s>>>(A.get(), m_len, lda, n, norms.get());
     FTT_LAUNCH();
     FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
   } else {
-    const bool td = sym_eig_tridiag(A.get(), n, V.get(), h, s, mixed);
-    note_eig(td);
+    const bool fast = sym_eig_fast(A.get(), n, V.get(), h, max_sweeps, s, mixed);
+    const bool td = fast || sym_eig_tridiag(A.get(), n, V.get(), h, s, mixed);
+    if (!fast) note_eig(td);
     if (td) out.sweeps = 0;
     else out.sweeps = mixed ? sym_eig_mixed32(A.get(), n, V.get(), h, max_sweeps, s)
                             : sym_eig_refined(A.get(), n, V.get(), h, max_sweeps, s);
@@ -1112,6 +1306,14 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
   }
 }
 
+bool sym_eig_fast(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps, cudaStream_t s,
+                  bool mixed) {
+  if (!sym_eig_start_f32(G, n, V, lam_out, s)) return false;
+  if (!refine_eig(G, n, V, lam_out, max_sweeps, s, mixed)) return false;
+  note_eig_fast();
+  return true;
+}
+
 void sym_eig_iterative(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps,
                        cudaStream_t s) {
   sym_eig_refined(G, n, V, lam_out, max_sweeps, s);
@@ -1124,8 +1326,9 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
   const int n = (int)M;
   DBuf<double> V((size_t)n * n, s);
   std::vector<double> h(n);
-  const bool td = sym_eig_tridiag(Gram, n, V.get(), h, s, mixed);
-  note_eig(td);
+  const bool fast = sym_eig_fast(Gram, n, V.get(), h, max_sweeps, s, mixed);
+  const bool td = fast || sym_eig_tridiag(Gram, n, V.get(), h, s, mixed);
+  if (!fast) note_eig(td);
   if (td) out.sweeps = 0;
   else out.sweeps = mixed ? sym_eig_mixed32(Gram, n, V.get(), h, max_sweeps, s)
                           : sym_eig_refined(Gram, n, V.get(), h, max_sweeps, s);

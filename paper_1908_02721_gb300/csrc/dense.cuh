@@ -25,11 +25,15 @@ void gemm_f64_dfma(int64_t M, int64_t N, int64_t K, double alpha, const double* 
                    cudaStream_t s, bool sym = false);
 
 // The product on the tcgen05 tensor cores from exact bf16 slices of the operands
-// (gemm_ozaki.cu): slices = 7 gives FP64-level products, 3 FP32-level.  Returns
-// false (C untouched) when it does not apply or its kernel gave up.
+// (gemm_ozaki.cu): slices = 7 gives FP64-level products (8 slices of 7 bits), 3
+// FP32-level (3 slices of 8 bits).  Returns false (C untouched) when the shape does
+// not apply.  A kernel that gives up on a bounded wait sets a sticky device flag;
+// ozaki_take_timeout reads and clears it and fails with FASTTT_ETIMEOUT if set.
 bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai,
                 int64_t sak, const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci,
                 int64_t scj, cudaStream_t s, bool sym = false);
+
+void ozaki_take_timeout(cudaStream_t s);
 
 // Products below this many multiply-adds stay on the DFMA / mma.sync kernels.
 constexpr double kTensorGemmMin = 67108864.0;   // 2^26
@@ -54,6 +58,20 @@ inline void gemm(bool mixed, int64_t M, int64_t N, int64_t K, double alpha, cons
     return;
   gemm_tf32x3(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
 }
+
+// One-sided Jacobi SVD (Hestenes) of the column-major m x n A (leading dimension
+// lda): on return A V has orthogonal columns (A <- A V) and V (nv x n, column-major,
+// ldv; identity on entry) holds the rotations.  Returns the sweeps; ETIMEOUT when
+// the sweep bound is reached.
+int64_t jacobi_svd_f64(double* A, int64_t m, int64_t lda, int n, double* V, int64_t nv, int64_t ldv,
+                       int64_t max_sweeps, cudaStream_t s);
+
+// The same result for a tall A (lg >> n, n <= kMaxTsqrCols) through Householder
+// TSQR (tsqr.cu): Jacobi on the n x n R only, then A <- Q (R V).  A is lg x n
+// column-major with leading dimension lg.
+constexpr int kMaxTsqrCols = 64;
+bool tsqr_applies(int64_t lg, int n);
+int64_t tsqr_jacobi(double* A, int64_t lg, int n, double* V, int64_t max_sweeps, cudaStream_t s);
 
 // dst (cols x rows, row-major) = transpose of src (rows x cols, row-major)
 void transpose_f64(const double* src, int64_t rows, int64_t cols, double* dst, cudaStream_t s);
@@ -83,6 +101,21 @@ void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<in
 // the back-transformation GEMMs run split-TF32.  Returns false (V undefined)
 // when the route does not apply or its vectors could not be made orthonormal.
 bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed);
+
+// The FP32 start of the fast eigensolver (tridiag.cu): G scaled by a power of
+// two and rounded to FP32, FP32 Householder tridiagonalisation, bisection and
+// inverse iteration (subspace iteration with Gram-Schmidt on clusters of close
+// eigenvalues), back-transformation with FP32-level products.  V (row j = an
+// approximate eigenvector, FP64 storage) and approximate eigenvalues; false when
+// the route does not apply (a cluster larger than it handles, no cooperative launch).
+bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s);
+
+// Fast eigensolver: sym_eig_start_f32, then the Ogita-Aishima refinement with
+// FP64-level tensor-core products (mixed: FP32-level) and a Rayleigh-Ritz step on
+// runs of close eigenvalues.  Same layout as sym_eig_tridiag; false when a step
+// declines (the caller takes the FP64 tridiagonal route).
+bool sym_eig_fast(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps, cudaStream_t s,
+                  bool mixed);
 
 // The iterative eigensolver of the Gram route (FP32 Jacobi start, Ogita-Aishima
 // refinement, FP64 one-sided Jacobi polish); same layout as sym_eig_tridiag.

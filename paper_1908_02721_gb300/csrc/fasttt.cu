@@ -60,7 +60,7 @@ void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxe
 namespace {
 std::atomic<int64_t> g_block_sweeps{0};
 std::atomic<int> g_coop_err{0};
-std::atomic<int64_t> g_eig_tridiag{0}, g_eig_fallback{0};
+std::atomic<int64_t> g_eig_tridiag{0}, g_eig_fallback{0}, g_eig_fast{0};
 }  // namespace
 namespace {
 thread_local int g_gemm_engine = 0;
@@ -68,6 +68,7 @@ thread_local int g_gemm_engine = 0;
 void set_gemm_engine(int engine) { g_gemm_engine = engine; }
 int gemm_engine() { return g_gemm_engine; }
 void note_eig(bool tridiag) { (tridiag ? g_eig_tridiag : g_eig_fallback).fetch_add(1, std::memory_order_relaxed); }
+void note_eig_fast() { g_eig_fast.fetch_add(1, std::memory_order_relaxed); }
 void note_block_sweep(int err) {
   if (err) g_coop_err.store(err);
   else g_block_sweeps.fetch_add(1, std::memory_order_relaxed);
@@ -292,19 +293,26 @@ void finish_stats(fasttt_stats& st, int64_t launches0) {
   st.ms_tdeig = ms[KC_TDEIG];
   st.ms_gemm_oz = ms[KC_GEMM_OZ];
   st.flop_gemm_oz = work[KC_GEMM_OZ];
+  st.ms_tridiag32 = ms[KC_TRIDIAG32];
+  st.flop_tridiag32 = work[KC_TRIDIAG32];
+  st.ms_tsqr = ms[KC_TSQR];
+  st.flop_tsqr = work[KC_TSQR];
   kclock_reset();
   st.launches = launch_count() - launches0;
 }
 
 struct CounterSnap {
-  int64_t block_sweeps, eig_tridiag, eig_fallback;
+  int64_t block_sweeps, eig_tridiag, eig_fallback, eig_fast;
 };
-CounterSnap counter_snap() { return {block_sweep_count(), g_eig_tridiag.load(), g_eig_fallback.load()}; }
+CounterSnap counter_snap() {
+  return {block_sweep_count(), g_eig_tridiag.load(), g_eig_fallback.load(), g_eig_fast.load()};
+}
 void finish_block_stats(fasttt_stats& st, const CounterSnap& c0) {
   st.jacobi_block_sweeps = block_sweep_count() - c0.block_sweeps;
   st.coop_launch_error = last_coop_error();
   st.eig_tridiag = g_eig_tridiag.load() - c0.eig_tridiag;
   st.eig_fallbacks = g_eig_fallback.load() - c0.eig_fallback;
+  st.eig_fast = g_eig_fast.load() - c0.eig_fast;
 }
 
 double tail2(const std::vector<double>& s, int64_t r) {
@@ -591,6 +599,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   }
   st.ms_round = lap.lap();
   st.ms_total = total.lap();
+  ozaki_take_timeout(s);
   finish_stats(st, launches0);
   finish_block_stats(st, snap0);
 }
@@ -808,6 +817,48 @@ int fasttt_debug_gemm(int64_t M, int64_t N, int64_t K, const double* d_A, const 
     else if (!gemm_ozaki(engine == 1 ? 7 : 3, M, N, K, 1.0, d_A, K, 1, d_B, N, 1, 0.0, d_C, N, 1, s))
       fail(FASTTT_ENUMERIC, "tensor-core GEMM declined or gave up");
     FTT_CUDA(cudaStreamSynchronize(s));
+    ozaki_take_timeout(s);
+    return FASTTT_OK;
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
+}
+
+int fasttt_debug_svd(int64_t M, int64_t N, const double* d_Z, double* h_sigma, double* d_U, double* d_Vt,
+                     int precision, void* stream) {
+  try {
+    if (M < 1 || N < 1 || !d_Z || !h_sigma || !d_U || !d_Vt ||
+        (precision != FASTTT_PREC_FP64 && precision != FASTTT_PREC_MIXED))
+      fail(FASTTT_EINVAL, "fasttt_debug_svd: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    set_gemm_engine(FASTTT_GEMM_TENSOR);
+    SvdOut sv;
+    svd_truncated(d_Z, M, N, [](const std::vector<double>& sg) { return (int64_t)sg.size(); }, 200, sv, s,
+                  precision == FASTTT_PREC_MIXED, 0);
+    const int64_t r = sv.r;
+    FTT_CUDA(cudaMemcpyAsync(d_U, sv.U.get(), sizeof(double) * M * r, cudaMemcpyDeviceToDevice, s));
+    FTT_CUDA(cudaMemcpyAsync(d_Vt, sv.Vt.get(), sizeof(double) * r * N, cudaMemcpyDeviceToDevice, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    ozaki_take_timeout(s);
+    std::copy(sv.sigma_all.begin(), sv.sigma_all.begin() + r, h_sigma);
+    return FASTTT_OK;
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
+}
+
+int fasttt_debug_gram(int64_t M, int64_t K, const double* d_A, double* d_C, int engine, void* stream) {
+  try {
+    if (M < 1 || K < 1 || !d_A || !d_C || engine < 0 || engine > 3)
+      fail(FASTTT_EINVAL, "fasttt_debug_gram: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // A(i, k) = A[i K + k], B(k, j) = A[j K + k]
+    if (engine == 0) gemm_f64_dfma(M, M, K, 1.0, d_A, K, 1, d_A, 1, K, 0.0, d_C, M, 1, s, true);
+    else if (engine == 3) gemm_tf32x3(M, M, K, 1.0, d_A, K, 1, d_A, 1, K, 0.0, d_C, M, 1, s, true);
+    else if (!gemm_ozaki(engine == 1 ? 7 : 3, M, M, K, 1.0, d_A, K, 1, d_A, 1, K, 0.0, d_C, M, 1, s, true))
+      fail(FASTTT_ENUMERIC, "tensor-core GEMM declined or gave up");
+    FTT_CUDA(cudaStreamSynchronize(s));
+    ozaki_take_timeout(s);
     return FASTTT_OK;
   } catch (const Error& e) {
     return handle_error(e);
@@ -816,15 +867,18 @@ int fasttt_debug_gemm(int64_t M, int64_t N, int64_t K, const double* d_A, const 
 
 int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_lam, int method, void* stream) {
   try {
-    if (!d_G || !d_V || !h_lam || n < 1 || n > INT32_MAX / 2 || method < 0 || method > 2)
+    if (!d_G || !d_V || !h_lam || n < 1 || n > INT32_MAX / 2 || method < 0 || method > 3)
       fail(FASTTT_EINVAL, "fasttt_debug_sym_eig: bad argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<double> lam;
     bool ok = false;
-    if (method != 1) ok = sym_eig_tridiag(d_G, (int)n, d_V, lam, s, false);
+    if (method == 2 || method == 3) ok = sym_eig_fast(d_G, (int)n, d_V, lam, 40, s, false);
+    if (!ok && method == 3) fail(FASTTT_ENUMERIC, "fast route declined");
+    if (!ok && method != 1) ok = sym_eig_tridiag(d_G, (int)n, d_V, lam, s, false);
     if (!ok && method == 0) fail(FASTTT_ENUMERIC, "tridiagonal route declined");
     if (!ok) sym_eig_iterative(d_G, (int)n, d_V, lam, 40, s);
     FTT_CUDA(cudaStreamSynchronize(s));
+    ozaki_take_timeout(s);
     std::copy(lam.begin(), lam.end(), h_lam);
     return FASTTT_OK;
   } catch (const Error& e) {

@@ -1,31 +1,32 @@
 // Dense GEMM on the 5th-generation tensor cores (tcgen05, sm_103a) with FP64
 // operands, by exact bf16 slicing (the error-free splitting of Ozaki, Ogita,
-// Oishi & Rump, Numer. Algorithms 59, 2012):
+// Oishi & Rump, Numer. Algorithms 59, 2012), with b bits per slice:
 //
-//   row i of A:    a_ik = 2^{e_i} sum_{s=1..S} q^A_{s,ik} 2^{-8s},  |q^A_{s,ik}| <= 256 (s = 1), <= 128 (s > 1)
-//   column j of B: b_kj = 2^{f_j} sum_{t=1..S} q^B_{t,kj} 2^{-8t} + (truncation below 2^{-8S})
+//   row i of A:    a_ik = 2^{e_i} sum_{s=1..S} q^A_{s,ik} 2^{-bs},  |q_1| <= 2^b, |q_s| <= 2^{b-1} (s > 1)
+//   column j of B: b_kj = 2^{f_j} sum_{t=1..S} q^B_{t,kj} 2^{-bt}   (+ rounding below 2^{-bS-1})
 //
 // Every slice q is an integer of at most 8 significant bits, exact in bf16, and
 // every product q^A q^B is exact in FP32.  Products are grouped by level
-// g = s + t (g <= S + 1; the rest is below 2^{-8S} of |a||b|):
-//   (A B)_ij = 2^{e_i + f_j} sum_g 2^{-8g} sum_{s+t=g} sum_k q^A_{s,ik} q^B_{t,kj}.
-// One tcgen05.mma (kind::f16, bf16 x bf16 -> FP32 in TMEM) per slice pair and
-// K step of 16 accumulates a level over a K chunk of 64.  The first slice is at
-// most 256 in magnitude and the others at most 128, so a product is at most 2^16
-// (pair (1,1)) or 2^15, and a level's chunk sum over 64 products of at most S
-// pairs stays below 2^24: every level's chunk sum is exact in FP32.  After every chunk the 4 epilogue warps read the level
-// accumulators out of TMEM (tcgen05.ld) and add them into 64-bit
-// integer registers: the level sums are exact integers below 2^24, so levels
-// 2..5 are packed into one int64 (weights 2^{8(5-g)}) and the rest into another,
-// and the whole K reduction is exact; FP64 enters only when the two packed sums
-// are scaled into C.  S = 7 gives products to FP64 accuracy (levels below
-// 2^{-56}); S = 3 gives FP32-level accuracy (the mixed-precision path).
+// g = s + t (g <= S + 1; the rest is below 2^{-bS} of |a||b|):
+//   (A B)_ij = 2^{e_i + f_j} sum_g 2^{-bg} sum_{s+t=g} sum_k q^A_{s,ik} q^B_{t,kj}.
+// One tcgen05.mma (kind::f16, bf16 x bf16 -> FP32 in TMEM) per slice pair and K
+// step of 16 accumulates a level.  A level's sum over a window of KD values of k
+// is an integer below 2^24 (checked at compile time from the digit bounds), so it
+// is exact in FP32; after every window the 8 warps read the level accumulators
+// out of TMEM (tcgen05.ld) into 64-bit integer registers, packed four levels to an
+// integer, and the whole K reduction is exact.  FP64 enters only when the packed
+// sums are scaled into C.  FP64-level products: S = 8 slices of b = 7 bits
+// (levels below 2^{-63} dropped), windows of 256.  FP32-level products (mixed
+// precision): S = 3 slices of b = 8 bits, windows of 128.
 //
-// Tiles: 128 (M) x 64 (N) per CTA, K chunk 64 = one 128-byte bf16 row; the S
-// slices of A and of B for a chunk are loaded by TMA (SWIZZLE_128B, one box per
-// slice) into shared memory and consumed by K-major SW128 UMMA descriptors.
-// Every mbarrier wait is bounded; a block that gives up raises the error flag,
-// frees its TMEM and returns, and the caller falls back to the FP64 DFMA GEMM.
+// Tiles: 128 (M) x 64 (N) per CTA; K in stages of 32 (64-byte bf16 rows) through
+// a two-deep shared-memory ring, the S slices of A and of B of a stage loaded by
+// TMA (SWIZZLE_64B, one box per slice) and consumed by K-major SW64 UMMA
+// descriptors; the copy of stage k+1 is issued as soon as the MMAs of stage k-1
+// have released their buffer.  Every mbarrier wait is bounded; a block that gives
+// up raises a sticky device flag, waits (bounded) for its copies and MMAs in
+// flight, frees its TMEM and returns; the call that launched it then fails with
+// FASTTT_ETIMEOUT when the flag is read (ozaki_take_timeout, once per call).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -40,7 +41,12 @@ namespace fasttt {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 64, kBK = 64;
+constexpr int kBM = 128, kBN = 64, kBK = 64;   // kBK: K padding of the slices
+constexpr int kBKs = 32;                         // K per pipeline stage (64-byte rows)
+
+// Set by a block that gave up on a bounded wait; read and cleared by
+// ozaki_take_timeout (sticky across the calls in between, one per device).
+__device__ int g_oz_timeout = 0;
 constexpr long long kMbarSpins = 1ll << 22;
 constexpr int kThreads = 256;   // 8 warps: TMEM lane quarter warp % 4, column half warp / 4
 
@@ -76,14 +82,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// K-major operand tile of rows x 64 bf16 (128-byte rows), 128-byte swizzle:
-// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// K-major operand tile of rows x 32 bf16 (64-byte rows), 64-byte swizzle: 8-row
+// groups 512 bytes apart (stride byte offset), descriptor version 1, layout 4.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)(16u >> 4) << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)(512u >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)4 << 61;
   return d;
 }
 
@@ -118,30 +124,54 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// C tile (128 x 64) of alpha 2^{e_i + f_j} sum_g 2^{-8g} L_g + beta C.
-template <int S>
+// Largest level sum per k: level g collects the pairs s + t = g of digits bounded
+// by 2^BITS (the top one) and 2^{BITS-1} (the others).
+template <int S, int BITS>
+__host__ __device__ constexpr long long oz_level_max() {
+  long long mx = 0;
+  for (int g = 2; g <= S + 1; ++g) {
+    long long sum = 0;
+    for (int s = 1; s <= S; ++s) {
+      const int t = g - s;
+      if (t < 1 || t > S) continue;
+      sum += ((s == 1) ? (1ll << BITS) : (1ll << (BITS - 1))) * ((t == 1) ? (1ll << BITS) : (1ll << (BITS - 1)));
+    }
+    mx = sum > mx ? sum : mx;
+  }
+  return mx;
+}
+
+// C tile (128 x 64) of alpha 2^{e_i + f_j} sum_g 2^{-BITS g} L_g + beta C.  K runs
+// in stages of 32 through a two-deep shared-memory ring (TMA, SWIZZLE_64B); the
+// level sums accumulate in TMEM over windows of KD and are then drained exactly
+// into 64-bit integers (KD times the largest level sum per k stays below 2^24).
+template <int S, int BITS, int KD>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t M,
                       int64_t N, int64_t Kp, int64_t Mp, int64_t Np, const int* __restrict__ ea,
                       const int* __restrict__ fb, double alpha, double beta, double* __restrict__ C, int64_t sci,
-                      int64_t scj, bool sym, int* err) {
+                      int64_t scj, bool sym) {
+  static_assert((long long)KD * oz_level_max<S, BITS>() < (1ll << 24), "level sums of a window must stay exact");
+  static_assert(KD % kBKs == 0, "windows are whole stages");
   constexpr int kLevels = S;                       // g = 2 .. S + 1
   constexpr uint32_t kCols = (kLevels * kBN <= 256) ? 256 : 512;
-  constexpr uint32_t kTileA = kBM * kBK * 2, kTileB = kBN * kBK * 2;
+  constexpr uint32_t kTileA = kBM * kBKs * 2, kTileB = kBN * kBKs * 2;
   constexpr uint32_t kStageBytes = S * (kTileA + kTileB);
+  constexpr int kWindow = KD / kBKs;
   const int bm = blockIdx.x, bn = blockIdx.y;
   if (sym && (int64_t)bm * kBM >= (int64_t)(bn + 1) * kBN) return;   // strictly below the diagonal
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;                      // S tiles of 128 x 64 bf16
-  unsigned char* sB = smem + S * kTileA;         // S tiles of 64 x 64 bf16
-  __shared__ uint64_t full_bar, mma_bar;
+  __shared__ uint64_t full_bar[2], empty_bar[2], drain_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&full_bar, 1);
-    mbar_init(&mma_bar, 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&full_bar[q], 1);
+      mbar_init(&empty_bar[q], 1);
+    }
+    mbar_init(&drain_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -156,62 +186,72 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tbase = tmem_base;
   const uint32_t idesc = idesc_bf16(kBM, kBN);
-  // Exact integer accumulation of the level sums over K: levels 2..5 in hi (level
-  // g weighted 2^{8(5-g)}), levels 6..S+1 in lo (weighted 2^{8(S+1-g)}); a chunk
-  // adds below 2^48 to each, so 2^15 chunks fit in int64.
+  // Exact integer accumulation of the level sums over K: the first kHiLevels levels
+  // in hi (level g weighted 2^{BITS(kHiLevels+1-g)}), the rest in lo (weighted
+  // 2^{BITS(S+1-g)}); a window adds below 2^{24+3 BITS} to each.
   constexpr int kHiLevels = (S < 4) ? S : 4;
   constexpr int kLoLevels = S - kHiLevels;
   long long hi[32], lo[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0;
-  const int nchunks = (int)(Kp / kBK);
+  const int nk = (int)(Kp / kBKs);
   const int quarter = warp & 3, half = warp >> 2;
-  bool ok = true;
-  int pending = 0;             // 1: a TMA phase, 2: an MMA phase left unfinished by a timeout
-  uint32_t pending_parity = 0;
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&full_bar, kStageBytes);
-    for (int s = 0; s < S; ++s) {
-      tma_load_2d(sA + s * kTileA, &tmA, &full_bar, 0, (int)(s * Mp + (int64_t)bm * kBM));
-      tma_load_2d(sB + s * kTileB, &tmB, &full_bar, 0, (int)(s * Np + (int64_t)bn * kBN));
+  auto load_stage = [&](int st, int kc) {
+    unsigned char* base = smem + st * kStageBytes;
+    mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
+    for (int q = 0; q < S; ++q) {
+      tma_load_2d(base + q * kTileA, &tmA, &full_bar[st], kc * kBKs, (int)(q * Mp + (int64_t)bm * kBM));
+      tma_load_2d(base + S * kTileA + q * kTileB, &tmB, &full_bar[st], kc * kBKs, (int)(q * Np + (int64_t)bn * kBN));
     }
-  }
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const uint32_t parity = (uint32_t)(ch & 1);
-    if (!mbar_wait(&full_bar, parity)) abort_flag = 1;
-    if (__syncthreads_or(abort_flag)) { ok = false; pending = 1; pending_parity = parity; break; }
-    tc_fence_after();
-    if (tid == 0) {
-      // level g = s + t (g = 2 .. S + 1) accumulates in TMEM columns (g - 2) * 64 ..
-      uint32_t started = 0;   // bit l: level l already has a product in this chunk
+  };
+  // issuing thread's view of the copies in flight (for a clean exit after a timeout)
+  bool tma_pending[2] = {false, false};
+  uint32_t tma_phase[2] = {0, 0};
+  if (tid == 0)
+    for (int st = 0; st < 2 && st < nk; ++st) { load_stage(st, st); tma_pending[st] = true; }
+  bool ok = true;
+  uint32_t drain_phase = 0;
+  for (int w0 = 0; w0 < nk; w0 += kWindow) {
+    const int w1 = (w0 + kWindow < nk) ? w0 + kWindow : nk;
+    if (tid == 0 && !abort_flag) {
+      uint32_t started = 0;   // bit l: level l has a product in this window
+      for (int kc = w0; kc < w1; ++kc) {
+        const int st = kc & 1;
+        if (!mbar_wait(&full_bar[st], tma_phase[st])) { abort_flag = 1; break; }
+        tma_pending[st] = false;
+        tma_phase[st] ^= 1;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + st * kStageBytes), b0 = a0 + S * kTileA;
 #pragma unroll 1
-      for (int s = 1; s <= S; ++s) {
-        const uint64_t da = sw128_desc(smem_u32(sA + (s - 1) * kTileA));
+        for (int q = 1; q <= S; ++q) {
+          const uint64_t da = sw64_desc(a0 + (q - 1) * kTileA);
 #pragma unroll 1
-        for (int t = 1; t + s <= S + 1; ++t) {
-          const int l = s + t - 2;
-          const uint64_t db = sw128_desc(smem_u32(sB + (t - 1) * kTileB));
+          for (int t = 1; t + q <= S + 1; ++t) {
+            const int l = q + t - 2;
+            const uint64_t db = sw64_desc(b0 + (t - 1) * kTileB);
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {   // K steps of 16 bf16 = 32 bytes
-            umma_bf16(tbase + (uint32_t)(l * kBN), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
-                      (started >> l) & 1u);
-            started |= 1u << l;
+            for (int kk = 0; kk < kBKs / 16; ++kk) {   // K steps of 16 bf16 = 32 bytes
+              umma_bf16(tbase + (uint32_t)(l * kBN), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
+                        (started >> l) & 1u);
+              started |= 1u << l;
+            }
           }
         }
+        umma_commit(&empty_bar[st]);
+        // refill the other stage (consumed by step kc - 1) with step kc + 1
+        if (kc >= 1 && kc + 1 < nk) {
+          const int o = st ^ 1;
+          if (!mbar_wait(&empty_bar[o], (uint32_t)(((kc - 1) >> 1) & 1))) { abort_flag = 1; break; }
+          load_stage(o, kc + 1);
+          tma_pending[o] = true;
+        }
       }
-      umma_commit(&mma_bar);
+      if (!abort_flag) umma_commit(&drain_bar);
     }
-    if (!mbar_wait(&mma_bar, parity)) abort_flag = 1;
-    if (__syncthreads_or(abort_flag)) { ok = false; pending = 2; pending_parity = parity; break; }
+    const bool got = mbar_wait(&drain_bar, drain_phase);
+    if (__syncthreads_or(!got || abort_flag)) { ok = false; break; }
+    drain_phase ^= 1;
     tc_fence_after();
-    // the MMAs have read the stage: load the next chunk while this one drains
-    if (tid == 0 && ch + 1 < nchunks) {
-      mbar_arrive_expect_tx(&full_bar, kStageBytes);
-      for (int s = 0; s < S; ++s) {
-        tma_load_2d(sA + s * kTileA, &tmA, &full_bar, (ch + 1) * kBK, (int)(s * Mp + (int64_t)bm * kBM));
-        tma_load_2d(sB + s * kTileB, &tmB, &full_bar, (ch + 1) * kBK, (int)(s * Np + (int64_t)bn * kBN));
-      }
-    }
     // drain: TMEM lanes 32 * quarter .. (tile rows), columns 32 * half .. of every level
     const uint32_t lane_base = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
 #pragma unroll
@@ -221,11 +261,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t r[16];
         tmem_ld16(lane_base + (uint32_t)(l * kBN + c0), r);
         if (l < kHiLevels) {
-          const int sh = 8 * (kHiLevels - 1 - l);
+          const int sh = BITS * (kHiLevels - 1 - l);
 #pragma unroll
           for (int c = 0; c < 16; ++c) hi[c0 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
         } else {
-          const int sh = 8 * (kLevels - 1 - l);
+          const int sh = BITS * (kLevels - 1 - l);
 #pragma unroll
           for (int c = 0; c < 16; ++c) lo[c0 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
         }
@@ -236,24 +276,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (ok) {
     const int64_t i = (int64_t)bm * kBM + quarter * 32 + lane;
     if (i < M) {
-      const double si = ldexp(alpha, ea[i]);
-      // value = 2^{-8(kHiLevels+1)} hi + 2^{-8(S+1)} lo
-      const double whi = ldexp(1.0, -8 * (kHiLevels + 1)), wlo = ldexp(1.0, -8 * (S + 1));
+      // value = 2^{e_i + f_j} alpha (2^{-BITS(kHiLevels+1)} hi + 2^{-BITS(S+1)} lo)
+      const double whi = ldexp(1.0, -BITS * (kHiLevels + 1)), wlo = ldexp(1.0, -BITS * (S + 1));
+      const int ei = ea[i];
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int64_t j = (int64_t)bn * kBN + half * 32 + c;
         if (j >= N) continue;
         double* cp = C + i * sci + j * scj;
         const double sum = fma((double)hi[c], whi, (kLoLevels > 0) ? (double)lo[c] * wlo : 0.0);
-        const double v = ldexp(si * sum, fb[j]);
+        const double v = ldexp(alpha * sum, ei + fb[j]);
         *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
       }
     }
   } else {
-    // give the copies or MMAs still in flight a second bounded wait before TMEM is freed
-    if (pending == 1) mbar_wait(&full_bar, pending_parity);
-    if (pending == 2) mbar_wait(&mma_bar, pending_parity);
-    if (tid == 0) atomicOr(err, 1);
+    // give the copies and MMAs still in flight a bounded wait before TMEM is freed
+    if (tid == 0) {
+      for (int st = 0; st < 2; ++st)
+        if (tma_pending[st]) mbar_wait(&full_bar[st], tma_phase[st]);
+      umma_commit(&drain_bar);
+      mbar_wait(&drain_bar, drain_phase);
+      atomicOr(&g_oz_timeout, 1);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -261,38 +305,154 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols) : "memory");
 }
 
-// Row exponents and slices of A (M x K with element strides): e_i with
-// max_k |a_ik| < 2^{e_i}; q[s][i][k] (bf16, Mp x Kp per slice, zero padded).
-// One warp per row (of A, or of B^T for the B operand).
-template <int S>
-__global__ void ozaki_split_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t s_row,
-                                   int64_t s_col, int64_t rows_p, int64_t cols_p, int* __restrict__ ex,
-                                   __nv_bfloat16* __restrict__ q) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = w; i < rows_p; i += nw) {
-    double mx = 0.0;
-    if (i < rows)
-      for (int64_t k = lane; k < cols; k += 32) mx = fmax(mx, fabs(X[i * s_row + k * s_col]));
+// ------------------------------------------------------------------ splitting
+// Row i of an operand X (rows x cols, X(i, k) = X[i*s_row + k*s_col]) is split
+// as follows.  e_i is the exponent with max_k |x_ik| < 2^{e_i} (frexp's), and
+//   R_ik = round(x_ik 2^{8S - e_i})          (|R| <= 2^{8S}, an exact integer)
+// is written in balanced base-256 digits: the S-1 low digits d in [-128, 127]
+// and the top digit q_1 = (R - low part) / 2^{8(S-1)} with |q_1| <= 256, so that
+// x_ik 2^{-e_i} = sum_s q_s 2^{-8s} up to the dropped |x| 2^{-8S-1} rounding.
+// Everything is integer arithmetic on the bit pattern (no FP64 instruction):
+// the max of |x| is the max of the sign-cleared bits, R is the 53-bit
+// significand shifted into place, and a digit becomes bf16 exactly (at most 8
+// significant bits) through the FP32 pattern of a small integer.
+
+constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+
+// mx[i] = max over k of the sign-cleared bits of x_ik (atomic over column chunks;
+// mx zeroed by the caller).  by_row: rows are contiguous (s_row = 1), one thread
+// per row; otherwise one warp per row with the lanes along k.
+__global__ void oz_rowmax_kernel(const double* __restrict__ X, int64_t rows, int64_t cols, int64_t s_row,
+                                 int64_t s_col, int64_t kchunk, bool by_row, unsigned long long* __restrict__ mx) {
+  const int64_t k0 = (int64_t)blockIdx.y * kchunk;
+  const int64_t k1 = min(cols, k0 + kchunk);
+  unsigned long long m = 0;
+  if (by_row) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    for (int64_t k = k0; k < k1; ++k)
+      m = max(m, (unsigned long long)__double_as_longlong(__ldg(X + i + k * s_col)) & kAbsMask);
+    if (m) atomicMax(mx + i, m);
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= rows) return;
+    const double* row = X + i * s_row;
+    for (int64_t k = k0 + lane; k < k1; k += 32)
+      m = max(m, (unsigned long long)__double_as_longlong(__ldg(row + k * s_col)) & kAbsMask);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) {
-      frexp(mx, &e);   // mx = m 2^e, 0.5 <= m < 1: mx < 2^e
-    }
-    if (lane == 0 && i < rows) ex[i] = e;
-    for (int64_t k = lane; k < cols_p; k += 32) {
-      double r = (i < rows && k < cols) ? ldexp(X[i * s_row + k * s_col], -e) : 0.0;   // |r| < 1, exact
+    for (int o = 16; o > 0; o >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m) atomicMax(mx + i, m);
+  }
+}
+
+// frexp's exponent of the double with sign-cleared bits a (0 for zero).
+__device__ __forceinline__ int oz_exp(unsigned long long a) {
+  if (a == 0) return 0;
+  const int eb = (int)(a >> 52);
+  if (eb) return eb - 1022;                 // a in [2^{eb-1023}, 2^{eb-1022})
+  return (64 - __clzll((long long)a)) - 1074;   // subnormal: a = m 2^-1074
+}
+
+// The S balanced digits of x 2^{-e} (q[0] the top one), BITS bits per digit.
+template <int S, int BITS>
+__device__ __forceinline__ void oz_digits(double x, int e, int (&q)[S]) {
+  const long long b = __double_as_longlong(x);
+  const unsigned long long a = (unsigned long long)b & kAbsMask;
+  long long R = 0;
+  if (a != 0) {
+    const int eb = (int)(a >> 52);
+    const unsigned long long m = (a & 0xFFFFFFFFFFFFFull) | (eb ? (1ull << 52) : 0ull);
+    // |x| = m 2^{E}, E = max(eb, 1) - 1075;  R = round(m 2^{sh}), sh <= 8S - 53 for normal x
+    const int sh = (eb ? eb : 1) - 1075 + S * BITS - e;
+    unsigned long long u;
+    if (sh >= 0) u = m << sh;
+    else if (sh > -64) u = (m + (1ull << (-sh - 1))) >> (-sh);
+    else u = 0;
+    R = (b < 0) ? -(long long)u : (long long)u;
+  }
+  constexpr long long kHalf = 1ll << (BITS - 1), kMask = (1ll << BITS) - 1;
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const double t = r * 256.0;   // exact
-        const double qv = rint(t);    // |qv| <= 256
-        r = t - qv;                   // exact, |r| <= 1/2
-        q[((int64_t)s * rows_p + i) * cols_p + k] = __float2bfloat16_rn((float)qv);
+  for (int t = S - 1; t >= 1; --t) {
+    const long long dl = ((R + kHalf) & kMask) - kHalf;
+    q[t] = (int)dl;
+    R = (R - dl) >> BITS;   // exact: R - dl is a multiple of 2^BITS
+  }
+  q[0] = (int)R;
+}
+
+// bf16 bits of a small integer (|d| <= 2^8): exact through the FP32 pattern.
+__device__ __forceinline__ uint32_t oz_bf16_bits(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;   // 1.5 * 2^23 magic: exact for |d| < 2^22
+  return __float_as_uint(f) >> 16;
+}
+
+// Slices q[s][i][k] (bf16, rows_p x cols_p per slice, zero padded) and row
+// exponents ex[i], from the row maxima.  One 64 x 64 tile per block iteration:
+// loaded through shared memory along X's contiguous dimension, written along k.
+template <int S, int BITS>
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
+                                                       int64_t s_row, int64_t s_col, bool by_row, int64_t rows_p,
+                                                       int64_t cols_p, const unsigned long long* __restrict__ mx,
+                                                       int* __restrict__ ex, __nv_bfloat16* __restrict__ q) {
+  __shared__ double t[64][65];
+  __shared__ int es[64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tiles_c = cols_p / 64, ntiles = (rows_p / 64) * tiles_c;
+  uint32_t* q32 = reinterpret_cast<uint32_t*>(q);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = (tile / tiles_c) * 64, c0 = (tile % tiles_c) * 64;
+    if (by_row) {
+      for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+        const int cc = e >> 6, rr = e & 63;
+        const int64_t i = r0 + rr, k = c0 + cc;
+        t[rr][cc] = (i < rows && k < cols) ? __ldg(X + i + k * s_col) : 0.0;
+      }
+    } else {
+      for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+        const int rr = e >> 6, cc = e & 63;
+        const int64_t i = r0 + rr, k = c0 + cc;
+        t[rr][cc] = (i < rows && k < cols) ? __ldg(X + i * s_row + k * s_col) : 0.0;
       }
     }
+    if (threadIdx.x < 64) {
+      const int64_t i = r0 + threadIdx.x;
+      const int e = (i < rows) ? oz_exp(mx[i]) : 0;
+      es[threadIdx.x] = e;
+      if (c0 == 0 && i < rows) ex[i] = e;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int rr = warp * 8; rr < warp * 8 + 8; ++rr) {
+      const int e = es[rr];
+      int d0[S], d1[S];
+      oz_digits<S, BITS>(t[rr][2 * lane], e, d0);
+      oz_digits<S, BITS>(t[rr][2 * lane + 1], e, d1);
+      const int64_t base = ((r0 + rr) * cols_p + c0) / 2 + lane;
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl)
+        q32[(int64_t)sl * (rows_p * cols_p / 2) + base] = oz_bf16_bits(d0[sl]) | (oz_bf16_bits(d1[sl]) << 16);
+    }
+    __syncthreads();
   }
+}
+
+// Row exponents and slices of the operand X (see above).
+template <int S, int BITS>
+void oz_split(const double* X, int64_t rows, int64_t cols, int64_t s_row, int64_t s_col, int64_t rows_p,
+              int64_t cols_p, int* ex, __nv_bfloat16* q, cudaStream_t s) {
+  DBuf<unsigned long long> mx((size_t)rows, s);
+  FTT_CUDA(cudaMemsetAsync(mx.get(), 0, mx.bytes(), s));
+  const bool by_row = (s_row == 1 && s_col != 1);
+  int64_t kchunk = by_row ? 256 : 2048;
+  kchunk = std::max<int64_t>(kchunk, ceil_div(cols, 65535));
+  const dim3 g1((unsigned)(by_row ? ceil_div(rows, 256) : ceil_div(rows, 8)), (unsigned)ceil_div(cols, kchunk));
+  oz_rowmax_kernel<<<g1, 256, 0, s>>>(X, rows, cols, s_row, s_col, kchunk, by_row, mx.get());
+  FTT_LAUNCH();
+  const int64_t ntiles = (rows_p / 64) * (cols_p / 64);
+  oz_slice_kernel<S, BITS><<<(unsigned)std::min<int64_t>(ntiles, (int64_t)kNumSMs * 8), 256, 0, s>>>(
+      X, rows, cols, s_row, s_col, by_row, rows_p, cols_p, mx.get(), ex, q);
+  FTT_LAUNCH();
 }
 
 __global__ void mirror_upper_oz_kernel(double* C, int64_t n) {
@@ -322,50 +482,47 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols_p, in
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols_p, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)cols_p * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)kBKs, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int S>
+template <int S, int BITS, int KD>
 bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
                const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
                cudaStream_t s, bool sym) {
   const int64_t Mp = ceil_div(M, kBM) * kBM, Np = ceil_div(N, kBN) * kBN, Kp = ceil_div(K, kBK) * kBK;
-  if ((S * Mp) >= INT32_MAX || (S * Np) >= INT32_MAX || Np / kBN > 65535) return false;
-  if (Kp / kBK > (1 << 15)) return false;   // the int64 level accumulators hold 2^15 chunks
-  const size_t smem = (size_t)S * (kBM + kBN) * kBK * 2 + 1024;
+  if ((S * Mp) >= INT32_MAX || (S * Np) >= INT32_MAX || Np / kBN > 65535 || Kp >= INT32_MAX) return false;
+  // the int64 level accumulators take 2^{37 - 3 BITS} windows
+  if (ceil_div(Kp, KD) > (1ll << (37 - 3 * BITS))) return false;
+  const size_t smem = 2 * (size_t)S * (kBM + kBN) * kBKs * 2 + 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(ozaki_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(ozaki_gemm_kernel<S, BITS, KD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
     attr_set = true;
   }
-  DBuf<__nv_bfloat16> qa((size_t)S * Mp * Kp, s), qb((size_t)S * Np * Kp, s);
-  DBuf<int> ea(Mp, s), fb(Np, s), err(1, s);
-  FTT_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-  // A rows: a(i, k) = A[i*sai + k*sak]; B^T rows: b(j, k) = B[k*sbk + j*sbj]
-  ozaki_split_kernel<S><<<grid_for(Mp * 32), 256, 0, s>>>(A, M, K, sai, sak, Mp, Kp, ea.get(), qa.get());
-  FTT_LAUNCH();
-  ozaki_split_kernel<S><<<grid_for(Np * 32), 256, 0, s>>>(B, N, K, sbj, sbk, Np, Kp, fb.get(), qb.get());
-  FTT_LAUNCH();
+  const bool same = (A == B && M == N && sai == sbj && sak == sbk);
+  DBuf<__nv_bfloat16> qa((size_t)S * Mp * Kp, s), qb(same ? 0 : (size_t)S * Np * Kp, s);
+  DBuf<int> ea(Mp, s), fb(same ? 0 : Np, s);
+  // A rows: a(i, k) = A[i*sai + k*sak]; B^T rows: b(j, k) = B[k*sbk + j*sbj].  When B^T is
+  // A itself (a Gram product) its slices are A's, padded to Mp >= Np rows.
+  oz_split<S, BITS>(A, M, K, sai, sak, Mp, Kp, ea.get(), qa.get(), s);
+  if (!same) oz_split<S, BITS>(B, N, K, sbj, sbk, Np, Kp, fb.get(), qb.get(), s);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, qa.get(), S * Mp, Kp, kBM) || !make_map(&mb, qb.get(), S * Np, Kp, kBN)) return false;
+  if (!make_map(&ma, qa.get(), S * Mp, Kp, kBM)) return false;
+  if (same ? !make_map(&mb, qa.get(), S * Mp, Kp, kBN) : !make_map(&mb, qb.get(), S * Np, Kp, kBN)) return false;
   KClock clk;
   kclock_begin(clk, KC_GEMM_OZ, s);
-  ozaki_gemm_kernel<S><<<dim3((unsigned)(Mp / kBM), (unsigned)(Np / kBN)), kThreads, smem, s>>>(
-      ma, mb, M, N, Kp, Mp, Np, ea.get(), fb.get(), alpha, beta, C, sci, scj, sym, err.get());
+  ozaki_gemm_kernel<S, BITS, KD><<<dim3((unsigned)(Mp / kBM), (unsigned)(Np / kBN)), kThreads, smem, s>>>(
+      ma, mb, M, N, Kp, Mp, same ? Mp : Np, ea.get(), same ? ea.get() : fb.get(), alpha, beta, C, sci, scj, sym);
   FTT_LAUNCH();
   kclock_end(clk, (sym ? 1.0 : 2.0) * (double)M * (double)N * (double)K, s);
-  int herr = 0;
-  FTT_CUDA(cudaMemcpyAsync(&herr, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-  FTT_CUDA(cudaStreamSynchronize(s));
-  if (herr) return false;
   if (sym) {
     mirror_upper_oz_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M);
     FTT_LAUNCH();
@@ -375,14 +532,28 @@ bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
 
 }  // namespace
 
+void ozaki_take_timeout(cudaStream_t s) {
+  int h = 0;
+  const int zero = 0;
+  FTT_CUDA(cudaMemcpyFromSymbolAsync(&h, g_oz_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    FTT_CUDA(cudaMemcpyToSymbolAsync(g_oz_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    fail(FASTTT_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up");
+  }
+}
+
 bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
                 const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
                 cudaStream_t s, bool sym) {
   if (M <= 0 || N <= 0) return true;
   if (sym && (M != N || sci != N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
   if (K <= 0) return false;
-  if (slices == 7) return run_ozaki<7>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
-  if (slices == 3) return run_ozaki<3>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  // FP64 level: 8 slices of 7 bits (level sums exact over windows of 256);
+  // FP32 level: 3 slices of 8 bits (windows of 128)
+  if (slices == 7) return run_ozaki<8, 7, 256>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  if (slices == 3) return run_ozaki<3, 8, 128>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
   return false;
 }
 

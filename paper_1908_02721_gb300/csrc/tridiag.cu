@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "dense.cuh"
@@ -30,61 +31,85 @@ namespace fasttt {
 namespace {
 
 constexpr int kWYBlock = 64;
+constexpr int kClusterMax = 256;   // largest eigenvalue cluster of the FP32 start
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-    tridiag_kernel(double* A, int64_t n, double* d, double* e, double* tau, double* p, unsigned* bar) {
-  extern __shared__ double vs[];   // the current reflector v (v_0 = 1)
+    tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* p, unsigned* bar) {
+  extern __shared__ __align__(16) unsigned char vs_raw[];
+  T* vs = reinterpret_cast<T*>(vs_raw);   // the current reflector v (v_0 = 1)
+  T* ws = vs + n;                         // w = p - (tau/2)(p.v) v
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + warp, W = (int64_t)gridDim.x * 8;
   unsigned gen = 0;
   for (int64_t k = 0; k + 2 < n; ++k) {
     const int64_t m = n - k - 1;
-    const double* x = A + k * n + k + 1;   // A[k, k+1:] = A[k+1:, k]
-    double s = 0.0, z1 = 0.0, z2 = 0.0;
+    const T* x = A + k * n + k + 1;   // A[k, k+1:] = A[k+1:, k]
+    T s = 0, z1 = 0, z2 = 0;
     for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) {
-      const double t = __ldcg(x + j);
+      const T t = __ldcg(x + j);
       s = fma(t, t, s);
     }
-    block_sum3<double>(s, z1, z2);
-    const double alpha = __ldcg(x);
-    double beta = alpha, tk = 0.0, scale = 0.0;
-    if (s > 0.0) {
+    block_sum3<T>(s, z1, z2);
+    const T alpha = __ldcg(x);
+    T beta = alpha, tk = 0, scale = 0;
+    if (s > T(0)) {
       beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
       tk = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+      scale = T(1) / (alpha - beta);
     }
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = (j == 0) ? 1.0 : __ldcg(x + j) * scale;
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = (j == 0) ? T(1) : __ldcg(x + j) * scale;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       d[k] = __ldcg(A + k * n + k);
       e[k] = beta;
       tau[k] = tk;
     }
-    // p = tau A22 v, one warp per row
+    // p = tau A22 v, one warp per row, four independent loads in flight per lane
     for (int64_t i = gw; i < m; i += W) {
-      const double* row = A + (k + 1 + i) * n + (k + 1);
-      double acc = 0.0;
-      for (int64_t j = lane; j < m; j += 32) acc = fma(__ldcg(row + j), vs[j], acc);
+      const T* row = A + (k + 1 + i) * n + (k + 1);
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      int64_t j = lane;
+      for (; j + 96 < m; j += 128) {
+        const T r0 = __ldcg(row + j), r1 = __ldcg(row + j + 32), r2 = __ldcg(row + j + 64), r3 = __ldcg(row + j + 96);
+        a0 = fma(r0, vs[j], a0);
+        a1 = fma(r1, vs[j + 32], a1);
+        a2 = fma(r2, vs[j + 64], a2);
+        a3 = fma(r3, vs[j + 96], a3);
+      }
+      for (; j < m; j += 32) a0 = fma(__ldcg(row + j), vs[j], a0);
+      T acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) p[i] = tk * acc;
     }
     if (!grid_barrier(bar, gridDim.x, gen)) return;
-    double pv = 0.0;
-    z1 = z2 = 0.0;
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) pv = fma(__ldcg(p + j), vs[j], pv);
-    block_sum3<double>(pv, z1, z2);
-    const double K = 0.5 * tk * pv;
-    if (tk != 0.0) {
+    T pv = 0;
+    z1 = z2 = 0;
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+      const T pj = __ldcg(p + j);
+      ws[j] = pj;
+      pv = fma(pj, vs[j], pv);
+    }
+    block_sum3<T>(pv, z1, z2);   // ends with a barrier: ws holds p
+    const T K = T(0.5) * tk * pv;
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) ws[j] = ws[j] - K * vs[j];
+    __syncthreads();
+    if (tk != T(0)) {
       for (int64_t i = gw; i < m; i += W) {
-        double* row = A + (k + 1 + i) * n + (k + 1);
-        const double vi = vs[i], wi = __ldcg(p + i) - K * vi;
-        for (int64_t j = lane; j < m; j += 32) {
-          const double vj = vs[j], wj = __ldcg(p + j) - K * vj;
-          row[j] = __ldcg(row + j) - vi * wj - wi * vj;
+        T* row = A + (k + 1 + i) * n + (k + 1);
+        const T vi = vs[i], wi = ws[i];
+        int64_t j = lane;
+        for (; j + 96 < m; j += 128) {
+          const T r0 = __ldcg(row + j), r1 = __ldcg(row + j + 32), r2 = __ldcg(row + j + 64), r3 = __ldcg(row + j + 96);
+          row[j] = r0 - vi * ws[j] - wi * vs[j];
+          row[j + 32] = r1 - vi * ws[j + 32] - wi * vs[j + 32];
+          row[j + 64] = r2 - vi * ws[j + 64] - wi * vs[j + 64];
+          row[j + 96] = r3 - vi * ws[j + 96] - wi * vs[j + 96];
         }
+        for (; j < m; j += 32) row[j] = __ldcg(row + j) - vi * ws[j] - wi * vs[j];
       }
     }
     if (blockIdx.x == 0)   // keep v in row k (columns k+1:) for the back-transformation
@@ -95,40 +120,75 @@ __global__ void __launch_bounds__(256)
     if (n >= 2) {
       d[n - 2] = __ldcg(A + (n - 2) * n + n - 2);
       e[n - 2] = __ldcg(A + (n - 2) * n + n - 1);
-      tau[n - 2] = 0.0;
+      tau[n - 2] = T(0);
     }
     d[n - 1] = __ldcg(A + (n - 1) * n + n - 1);
   }
 }
 
 // Number of eigenvalues of T (diagonal d, squared off-diagonal e2) below x.
-__device__ int sturm_count(const double* d, const double* e2, int64_t n, double x, double pivmin) {
+template <typename T>
+__device__ int sturm_count(const T* d, const T* e2, int64_t n, T x, T pivmin) {
   int c = 0;
-  double q = d[0] - x;
+  T q = d[0] - x;
   if (fabs(q) <= pivmin) q = -pivmin;
-  if (q < 0.0) ++c;
+  if (q < T(0)) ++c;
   for (int64_t i = 1; i < n; ++i) {
     q = (d[i] - x) - e2[i - 1] / q;
     if (fabs(q) <= pivmin) q = -pivmin;
-    if (q < 0.0) ++c;
+    if (q < T(0)) ++c;
   }
   return c;
 }
 
 // lam[j] = the j-th smallest eigenvalue (j = 0..n-1) by bisection of [gl, gu]
 // down to abstol or adjacent doubles (at most 128 halvings).
-__global__ void bisect_kernel(const double* d, const double* e2, int64_t n, double gl, double gu, double pivmin,
-                              double abstol, double* lam) {
+template <typename T>
+__global__ void bisect_kernel(const T* d, const T* e2, int64_t n, T gl, T gu, T pivmin, T abstol, T* lam) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    double lo = gl, hi = gu;
+    T lo = gl, hi = gu;
     for (int it = 0; it < 128; ++it) {
-      const double mid = 0.5 * (lo + hi);
+      const T mid = T(0.5) * (lo + hi);
       if (!(mid > lo && mid < hi) || hi - lo <= abstol) break;
       if (sturm_count(d, e2, n, mid, pivmin) > j) hi = mid;
       else lo = mid;
     }
-    lam[j] = 0.5 * (lo + hi);
+    lam[j] = T(0.5) * (lo + hi);
   }
+}
+
+// Multisection: a group of G lanes (G divides 32) per eigenvalue j probes G
+// points splitting [lo, hi] into G + 1 equal parts; the Sturm counts (warp ballot)
+// select the part that holds the j-th smallest eigenvalue.  Same result as
+// bisection (down to abstol or adjacent floating-point values) in
+// log_{G+1} instead of log_2 steps.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) multisect_kernel(const T* d, const T* e2, int64_t n, T gl, T gu, T pivmin,
+                                                        T abstol, T* lam) {
+  const int lane = threadIdx.x & 31, grp = lane / G, sub = lane % G;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t j = warp_id * (32 / G) + grp;
+  T lo = gl, hi = gu;
+  bool done = (j >= n);
+  for (int it = 0; it < 64; ++it) {
+    if (!done) {
+      const T mid = T(0.5) * (lo + hi);
+      if (!(mid > lo && mid < hi) || hi - lo <= abstol) done = true;
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+    const T x = lo + (hi - lo) * (T)(sub + 1) / (T)(G + 1);
+    const bool above = done ? false : (sturm_count(d, e2, n, x, pivmin) > j);
+    const unsigned ball = __ballot_sync(0xffffffffu, above);
+    if (!done) {
+      const unsigned gm = (G == 32) ? ball : ((ball >> (grp * G)) & ((1u << G) - 1u));
+      const int first = gm ? (__ffs(gm) - 1) : G;   // first probe above the eigenvalue
+      const T nlo = (first == 0) ? lo : lo + (hi - lo) * (T)first / (T)(G + 1);
+      const T nhi = (first == G) ? hi : lo + (hi - lo) * (T)(first + 1) / (T)(G + 1);
+      if (!(nlo >= lo && nhi <= hi && nlo < nhi)) done = true;
+      else { lo = nlo; hi = nhi; }
+    }
+  }
+  if (j < n && sub == 0) lam[j] = T(0.5) * (lo + hi);
 }
 
 __device__ __forceinline__ double start_component(int64_t i, int64_t j) {
@@ -142,34 +202,77 @@ __device__ __forceinline__ double start_component(int64_t i, int64_t j) {
 // Inverse iteration: thread t computes the eigenvector of T for shift lam[j0 + t]
 // into column j0 + t of Z (n x ldz row-major).  T - lambda I = P L U with partial
 // pivoting (tridiagonal LU with one fill-in diagonal); scratch arrays are laid
-// out [i * nv + t] so that a warp's accesses are contiguous.
-__global__ void inverse_iteration_kernel(const double* d, const double* e, int64_t n, const double* shift, int64_t j0,
-                                         int64_t nv, double pert, double* sdd, double* sdu, double* sdu2, double* sdl,
-                                         unsigned char* spiv, double* Z, int64_t ldz) {
+// out [i * nv + t] so that a warp's accesses are contiguous.  The factors stay in
+// the scratch arrays (further solves: tri_solve).
+#define S(a, i) a[(int64_t)(i) * nv + t]
+template <typename T>
+__device__ void tri_solve(int64_t n, int64_t nv, int64_t t, const T* sdd, const T* sdu, const T* sdu2, const T* sdl,
+                          const unsigned char* spiv, T* z, int64_t ldz) {
+  // L: the running value stays in a register; the loads do not depend on it
+  T carry = z[0];
+#pragma unroll 4
+  for (int64_t i = 0; i + 1 < n; ++i) {
+    T bn = z[(i + 1) * ldz];
+    if (S(spiv, i)) { const T tmp = carry; carry = bn; bn = tmp; }
+    z[i * ldz] = carry;
+    carry = bn - S(sdl, i) * carry;
+  }
+  z[(n - 1) * ldz] = carry;
+  // U (sdd holds the reciprocals of the pivots)
+  T v1 = 0, v2 = 0;
+#pragma unroll 4
+  for (int64_t i = n - 1; i >= 0; --i) {
+    T v = z[i * ldz];
+    if (i + 1 < n) v -= S(sdu, i) * v1;
+    if (i + 2 < n) v -= S(sdu2, i) * v2;
+    v *= S(sdd, i);
+    z[i * ldz] = v;
+    v2 = v1;
+    v1 = v;
+  }
+}
+
+template <typename T>
+__device__ void normalise_col(int64_t n, T* z, int64_t ldz) {
+  T mx = 0;
+  for (int64_t i = 0; i < n; ++i) mx = fmax(mx, fabs(z[i * ldz]));
+  if (!(mx > T(0)) || !isfinite(mx)) mx = T(1);
+  T nrm = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const T v = z[i * ldz] / mx;
+    nrm = fma(v, v, nrm);
+  }
+  const T inv = T(1) / (mx * sqrt(nrm));
+  for (int64_t i = 0; i < n; ++i) z[i * ldz] *= inv;
+}
+
+template <typename T>
+__global__ void inverse_iteration_kernel(const T* d, const T* e, int64_t n, const T* shift, int64_t j0, int64_t nv,
+                                         T pert, T* sdd, T* sdu, T* sdu2, T* sdl, unsigned char* spiv, T* Z,
+                                         int64_t ldz) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nv) return;
   const int64_t j = j0 + t;
-  const double lam = shift[j];
-#define S(a, i) a[(int64_t)(i) * nv + t]
+  const T lam = shift[j];
   for (int64_t i = 0; i < n; ++i) {
     S(sdd, i) = d[i] - lam;
     if (i + 1 < n) { S(sdu, i) = e[i]; S(sdl, i) = e[i]; }
-    S(sdu2, i) = 0.0;
+    S(sdu2, i) = T(0);
   }
   for (int64_t i = 0; i + 1 < n; ++i) {
-    const double di = S(sdd, i), li = S(sdl, i);
+    const T di = S(sdd, i), li = S(sdl, i);
     if (fabs(di) >= fabs(li)) {
-      const double piv = (di == 0.0) ? pert : di;
+      const T piv = (di == T(0)) ? pert : di;
       S(sdd, i) = piv;
-      const double f = li / piv;
+      const T f = li / piv;
       S(sdl, i) = f;
       S(sdd, i + 1) = S(sdd, i + 1) - f * S(sdu, i);
       S(spiv, i) = 0;
     } else {
-      const double f = di / li;
+      const T f = di / li;
       S(sdd, i) = li;
       S(sdl, i) = f;
-      const double u = S(sdu, i);
+      const T u = S(sdu, i);
       S(sdu, i) = S(sdd, i + 1);
       S(sdd, i + 1) = u - f * S(sdd, i + 1);
       if (i + 2 < n) {
@@ -179,37 +282,75 @@ __global__ void inverse_iteration_kernel(const double* d, const double* e, int64
       S(spiv, i) = 1;
     }
   }
-  if (fabs(S(sdd, n - 1)) < pert) S(sdd, n - 1) = copysign(pert, S(sdd, n - 1));
-  for (int64_t i = 0; i < n; ++i)
-    if (fabs(S(sdd, i)) < pert) S(sdd, i) = copysign(pert, S(sdd, i));
-  double* z = Z + j;
-  for (int64_t i = 0; i < n; ++i) z[i * ldz] = start_component(i, j);
-  for (int it = 0; it < 3; ++it) {
-    for (int64_t i = 0; i + 1 < n; ++i) {   // L
-      double bi = z[i * ldz], bn = z[(i + 1) * ldz];
-      if (S(spiv, i)) { const double tmp = bi; bi = bn; bn = tmp; }
-      z[i * ldz] = bi;
-      z[(i + 1) * ldz] = bn - S(sdl, i) * bi;
-    }
-    for (int64_t i = n - 1; i >= 0; --i) {   // U
-      double v = z[i * ldz];
-      if (i + 1 < n) v -= S(sdu, i) * z[(i + 1) * ldz];
-      if (i + 2 < n) v -= S(sdu2, i) * z[(i + 2) * ldz];
-      z[i * ldz] = v / S(sdd, i);
-    }
-    double mx = 0.0;
-    for (int64_t i = 0; i < n; ++i) mx = fmax(mx, fabs(z[i * ldz]));
-    if (!(mx > 0.0) || !isfinite(mx)) mx = 1.0;
-    double nrm = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-      const double v = z[i * ldz] / mx;
-      nrm = fma(v, v, nrm);
-    }
-    const double inv = 1.0 / (mx * sqrt(nrm));
-    for (int64_t i = 0; i < n; ++i) z[i * ldz] *= inv;
+  for (int64_t i = 0; i < n; ++i) {
+    T piv = S(sdd, i);
+    if (fabs(piv) < pert) piv = copysign(pert, piv);
+    S(sdd, i) = T(1) / piv;   // the solves multiply by the reciprocal pivots
   }
-#undef S
+  T* z = Z + j;
+  for (int64_t i = 0; i < n; ++i) z[i * ldz] = (T)start_component(i, j);
+  for (int it = 0; it < 3; ++it) {
+    tri_solve<T>(n, nv, t, sdd, sdu, sdu2, sdl, spiv, z, ldz);
+    normalise_col<T>(n, z, ldz);
+  }
 }
+
+// Clusters of close eigenvalues (block q: columns c0[2q] .. c0[2q+1]-1 of Z; the factors of every column in the scratch arrays, nv = n): subspace
+// iteration on the cluster, i.e. modified Gram-Schmidt of the cluster's columns
+// (twice), one more solve per column, and a final Gram-Schmidt.  Inverse
+// iteration alone returns nearly parallel vectors for eigenvalues closer than
+// its working accuracy; the cluster's span is still its invariant subspace.
+template <typename T>
+__global__ void __launch_bounds__(256) cluster_orth_kernel(const int32_t* c0, int64_t n, int64_t nv, const T* sdd,
+                                                           const T* sdu, const T* sdu2, const T* sdl,
+                                                           const unsigned char* spiv, T* Z, int64_t ldz) {
+  __shared__ T h[kClusterMax];
+  __shared__ T red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t a = c0[2 * blockIdx.x], b = c0[2 * blockIdx.x + 1];
+  auto gram_schmidt = [&]() {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int64_t k = a; k < b; ++k) {
+        T* zk = Z + k;
+        // h_j = z_j . z_k for the earlier columns of the cluster (a warp per column)
+        for (int64_t jj = a + warp; jj < k; jj += 8) {
+          const T* zj = Z + jj;
+          T acc = 0;
+          for (int64_t i = lane; i < n; i += 32) acc = fma(zj[i * ldz], zk[i * ldz], acc);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) h[jj - a] = acc;
+        }
+        __syncthreads();
+        T nrm = 0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+          T v = zk[i * ldz];
+          for (int64_t jj = a; jj < k; ++jj) v -= h[jj - a] * Z[i * ldz + jj];
+          zk[i * ldz] = v;
+          nrm = fma(v, v, nrm);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if (lane == 0) red[warp] = nrm;
+        __syncthreads();
+        T tot = 0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        const T inv = (tot > T(0)) ? T(1) / sqrt(tot) : T(0);
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) zk[i * ldz] *= inv;
+        __syncthreads();
+      }
+  };
+  for (int it = 0; it < 2; ++it) {
+    gram_schmidt();
+    for (int64_t t = a + threadIdx.x; t < b; t += blockDim.x) {
+      tri_solve<T>(n, nv, t, sdd, sdu, sdu2, sdl, spiv, Z + t, ldz);
+      normalise_col<T>(n, Z + t, ldz);
+    }
+    __syncthreads();
+  }
+  gram_schmidt();
+}
+#undef S
 
 // Vb (nr x kb row-major) = reflectors k0 .. k0+kb-1 on rows k0+1 .. n-1: column c
 // holds v_{k0+c} from row k0+c+1 on (stored in row k0+c of A), zeros above.
@@ -259,19 +400,24 @@ __global__ void __launch_bounds__(256) wy_gram_kernel(const double* __restrict__
 
 // T (kb x kb, upper triangular, row-major) of H_1 ... H_kb = I - V T V^T from
 // S = V^T V and the tau: T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] S[0:i, i].
-__global__ void wy_t_kernel(const double* S, const double* tau, int64_t kb, double* T) {
-  for (int64_t e = threadIdx.x; e < kb * kb; e += blockDim.x) T[e] = 0.0;
+// T lives in shared memory; four threads share each row's dot product.
+__global__ void __launch_bounds__(256) wy_t_kernel(const double* S, const double* tau, int64_t kb, double* T) {
+  __shared__ double sT[kWYBlock][kWYBlock + 1];
+  for (int e = threadIdx.x; e < kWYBlock * (kWYBlock + 1); e += blockDim.x) (&sT[0][0])[e] = 0.0;
   __syncthreads();
-  for (int64_t i = 0; i < kb; ++i) {
-    const double ti = tau[i];
-    if (threadIdx.x == 0) T[i * kb + i] = ti;
-    for (int64_t r = threadIdx.x; r < i; r += blockDim.x) {
-      double acc = 0.0;
-      for (int64_t c = r; c < i; ++c) acc = fma(T[r * kb + c], S[c * kb + i], acc);
-      T[r * kb + i] = -ti * acc;
-    }
+  const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+  for (int i = 0; i < (int)kb; ++i) {
+    const double ti = __ldg(tau + i);
+    double acc = 0.0;
+    if (r < i)
+      for (int c = r + q; c < i; c += 4) acc = fma(sT[r][c], __ldg(S + (int64_t)c * kb + i), acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (r < i && q == 0) sT[r][i] = -ti * acc;
+    if (threadIdx.x == 0) sT[i][i] = ti;
     __syncthreads();
   }
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) T[e] = sT[e / kb][e % kb];
 }
 
 __global__ void i_minus_sym_kernel(double* R, int64_t n) {
@@ -300,6 +446,57 @@ double frob2(const double* R, int64_t count, cudaStream_t s) {
   return t;
 }
 
+// Z <- Q Z for Q = H_0 ... H_{n-3} (reflector k stored in row k of A from column
+// k+1 on, v_0 = 1; tau on the device), blocks of kWYBlock reflectors from the
+// last to the first in the compact WY form I - V T V^T.  mixed: the two large
+// products of each block at FP32 level.
+void wy_back_transform(const double* A, const double* tau, int64_t n, double* Z, bool mixed, cudaStream_t s) {
+  const int64_t nrefl = n - 2;
+  if (nrefl < 1) return;
+  DBuf<double> Vb((size_t)(n - 1) * kWYBlock, s), S((size_t)kWYBlock * kWYBlock, s),
+      T((size_t)kWYBlock * kWYBlock, s), W1((size_t)kWYBlock * n, s), W2((size_t)kWYBlock * n, s);
+  for (int64_t k0 = ((nrefl - 1) / kWYBlock) * kWYBlock; k0 >= 0; k0 -= kWYBlock) {
+    const int64_t kb = std::min<int64_t>(kWYBlock, nrefl - k0), nr = n - k0 - 1;
+    wy_vectors_kernel<<<grid_for(nr * kb), 256, 0, s>>>(A, n, k0, kb, Vb.get());
+    FTT_LAUNCH();
+    FTT_CUDA(cudaMemsetAsync(S.get(), 0, sizeof(double) * kb * kb, s));
+    wy_gram_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nr, 64), kNumSMs)), 256, 0, s>>>(
+        Vb.get(), nr, kb, S.get());
+    FTT_LAUNCH();
+    wy_t_kernel<<<1, 256, 0, s>>>(S.get(), tau + k0, kb, T.get());
+    FTT_LAUNCH();
+    double* Zs = Z + (k0 + 1) * n;
+    gemm(mixed, kb, n, nr, 1.0, Vb.get(), 1, kb, Zs, n, 1, 0.0, W1.get(), n, 1, s);   // V^T Z
+    gemm_f64(kb, n, kb, 1.0, T.get(), kb, 1, W1.get(), n, 1, 0.0, W2.get(), n, 1, s);  // T (V^T Z)
+    gemm(mixed, nr, n, kb, -1.0, Vb.get(), kb, 1, W2.get(), n, 1, 1.0, Zs, n, 1, s);  // Z -= V T V^T Z
+  }
+}
+
+// max |x| over n doubles (sign-cleared bit patterns, atomic max; *out zeroed by the caller)
+__global__ void absmax_bits_kernel(const double* x, int64_t n, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+__global__ void scale_to_f32_kernel(const double* a, int64_t n, double sc, float* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)(a[i] * sc);
+}
+
+__global__ void f32_to_f64_kernel(const float* a, int64_t n, double* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+__global__ void identity64_kernel(double* V, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x)
+    V[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
 }  // namespace
 
 bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed) {
@@ -309,16 +506,16 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = sizeof(double) * (size_t)n;
+  const size_t smem = 2 * sizeof(double) * (size_t)n;
   if (!coop || smem + 4096 > (size_t)smem_max) return false;
   const int64_t nn = (int64_t)n * n;
   DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p(n, s);
   FTT_CUDA(cudaMemcpyAsync(A.get(), G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   // 1. tridiagonalisation
   {
-    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per = 0;
-    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel, 256, smem));
+    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<double>, 256, smem));
     const int grid = std::min(2, per) * sms;
     if (grid < 1) return false;
     DBuf<unsigned> bar(4, s);
@@ -329,7 +526,8 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
     void* args[] = {(void*)&Ap, (void*)&n64, (void*)&dp, (void*)&ep, (void*)&tp, (void*)&pp, (void*)&bp};
     KClock clk;
     kclock_begin(clk, KC_TRIDIAG, s);
-    const cudaError_t err = cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(grid), dim3(256), args, smem, s);
+    const cudaError_t err =
+        cudaLaunchCooperativeKernel((void*)tridiag_kernel<double>, dim3(grid), dim3(256), args, smem, s);
     if (err != cudaSuccess) {
       cudaGetLastError();
       return false;
@@ -366,7 +564,8 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   KClock clk2;
   kclock_begin(clk2, KC_TDEIG, s);
   const double abstol = 2.0 * 0x1p-53 * std::max(tnorm, 1e-300);   // the accuracy T carries from step 1
-  bisect_kernel<<<grid_for(n, 128), 128, 0, s>>>(d.get(), e2.get(), n, gl, gu, pivmin, abstol, lam.get());
+  multisect_kernel<double, 8><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(d.get(), e2.get(), n, gl, gu, pivmin, abstol,
+                                                                        lam.get());
   FTT_LAUNCH();
   std::vector<double> hl(n);
   FTT_CUDA(cudaMemcpyAsync(hl.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -410,29 +609,159 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
     }
     if (!ok) return false;
   }
-  // 5. X = Q Z, blocks of reflectors from the last to the first
-  {
-    const int64_t nrefl = n - 2;
-    DBuf<double> Vb((size_t)(n - 1) * kWYBlock, s), S((size_t)kWYBlock * kWYBlock, s),
-        T((size_t)kWYBlock * kWYBlock, s), W1((size_t)kWYBlock * n, s), W2((size_t)kWYBlock * n, s);
-    for (int64_t k0 = ((nrefl - 1) / kWYBlock) * kWYBlock; k0 >= 0; k0 -= kWYBlock) {
-      const int64_t kb = std::min<int64_t>(kWYBlock, nrefl - k0), nr = n - k0 - 1;
-      wy_vectors_kernel<<<grid_for(nr * kb), 256, 0, s>>>(A.get(), n, k0, kb, Vb.get());
-      FTT_LAUNCH();
-      FTT_CUDA(cudaMemsetAsync(S.get(), 0, sizeof(double) * kb * kb, s));
-      wy_gram_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nr, 64), kNumSMs)), 256, 0, s>>>(
-          Vb.get(), nr, kb, S.get());
-      FTT_LAUNCH();
-      wy_t_kernel<<<1, 64, 0, s>>>(S.get(), tau.get() + k0, kb, T.get());
-      FTT_LAUNCH();
-      double* Zs = Z.get() + (k0 + 1) * n;
-      gemm(mixed, kb, n, nr, 1.0, Vb.get(), 1, kb, Zs, n, 1, 0.0, W1.get(), n, 1, s);   // V^T Z
-      gemm_f64(kb, n, kb, 1.0, T.get(), kb, 1, W1.get(), n, 1, 0.0, W2.get(), n, 1, s);  // T (V^T Z)
-      gemm(mixed, nr, n, kb, -1.0, Vb.get(), kb, 1, W2.get(), n, 1, 1.0, Zs, n, 1, s);  // Z -= V T V^T Z
-    }
-  }
+  // 5. X = Q Z
+  wy_back_transform(A.get(), tau.get(), n, Z.get(), mixed, s);
   transpose_f64(Z.get(), n, n, V, s);   // V: column j = eigenvector j
   lam_out = hl;
+  return true;
+}
+
+
+bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s) {
+  if (n < 3) return false;
+  int dev = 0, coop = 0, sms = 0, smem_max = 0;
+  FTT_CUDA(cudaGetDevice(&dev));
+  FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t smem = 2 * sizeof(float) * (size_t)n;
+  const int64_t nn = (int64_t)n * n;
+  // every vector's tridiagonal factors are kept for the cluster iterations: 17 n^2 bytes
+  if (!coop || smem + 4096 > (size_t)smem_max || 17.0 * (double)nn > 6.0e9) return false;
+  // 0. G scaled by a power of two to max |g_ij| in [1/2, 1) (exact), rounded to FP32
+  double sc = 1.0;
+  {
+    DBuf<unsigned long long> mx(1, s);
+    FTT_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(unsigned long long), s));
+    absmax_bits_kernel<<<grid_for(nn), 256, 0, s>>>(G, nn, mx.get());
+    FTT_LAUNCH();
+    const unsigned long long bits = read_scalar(mx.get(), s);
+    double gmax;
+    std::memcpy(&gmax, &bits, sizeof(gmax));
+    if (!(gmax > 0.0)) {   // the zero matrix: V = I, all eigenvalues 0
+      identity64_kernel<<<grid_for(nn), 256, 0, s>>>(V, n);
+      FTT_LAUNCH();
+      lam_out.assign(n, 0.0);
+      return true;
+    }
+    int eg = 0;
+    std::frexp(gmax, &eg);
+    sc = std::ldexp(1.0, -eg);
+  }
+  DBuf<float> A(nn, s), d(n, s), e(n, s), tau(n, s), p(n, s);
+  scale_to_f32_kernel<<<grid_for(nn), 256, 0, s>>>(G, nn, sc, A.get());
+  FTT_LAUNCH();
+  // 1. FP32 tridiagonalisation
+  {
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 0;
+    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<float>, 256, smem));
+    const int grid = std::min(2, per) * sms;
+    if (grid < 1) return false;
+    DBuf<unsigned> bar(4, s);
+    FTT_CUDA(cudaMemsetAsync(bar.get(), 0, 4 * sizeof(unsigned), s));
+    int64_t n64 = n;
+    float *Ap = A.get(), *dp = d.get(), *ep = e.get(), *tp = tau.get(), *pp = p.get();
+    unsigned* bp = bar.get();
+    void* args[] = {(void*)&Ap, (void*)&n64, (void*)&dp, (void*)&ep, (void*)&tp, (void*)&pp, (void*)&bp};
+    KClock clk;
+    kclock_begin(clk, KC_TRIDIAG32, s);
+    const cudaError_t err =
+        cudaLaunchCooperativeKernel((void*)tridiag_kernel<float>, dim3(grid), dim3(256), args, smem, s);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    FTT_LAUNCH();
+    kclock_end(clk, 2.0 * (double)n * (double)n * (double)n, s);
+    unsigned hb[4];
+    FTT_CUDA(cudaMemcpyAsync(hb, bar.get(), sizeof(hb), cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    if (hb[2] != 0) return false;
+  }
+  std::vector<float> hd(n), he(n);
+  FTT_CUDA(cudaMemcpyAsync(hd.data(), d.get(), sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaMemcpyAsync(he.data(), e.get(), sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaStreamSynchronize(s));
+  // 2. eigenvalues of T by FP32 bisection (Gershgorin interval)
+  const double u32 = 0x1p-24;
+  double gl = INFINITY, gu = -INFINITY, emax2 = 0.0, tnorm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs((double)he[i - 1]) : 0.0) + (i + 1 < n ? fabs((double)he[i]) : 0.0);
+    gl = std::min(gl, (double)hd[i] - r);
+    gu = std::max(gu, (double)hd[i] + r);
+    tnorm = std::max(tnorm, fabs((double)hd[i]) + r);
+    if (i + 1 < n) emax2 = std::max(emax2, (double)he[i] * (double)he[i]);
+  }
+  if (!std::isfinite(gl) || !std::isfinite(gu) || !(tnorm > 0.0)) return false;
+  const double widen = 4.0 * u32 * tnorm * n;
+  gl -= widen;
+  gu += widen;
+  std::vector<float> he2(n, 0.0f);
+  for (int i = 0; i + 1 < n; ++i) he2[i] = he[i] * he[i];
+  DBuf<float> e2(n, s), lam(n, s), shift(n, s);
+  FTT_CUDA(cudaMemcpyAsync(e2.get(), he2.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  KClock clk2;
+  kclock_begin(clk2, KC_TDEIG, s);
+  const float pivmin = (float)(0x1p-126 * std::max(1.0, emax2));
+  multisect_kernel<float, 32><<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(d.get(), e2.get(), n, (float)gl, (float)gu,
+                                                                        pivmin, (float)(2.0 * u32 * tnorm), lam.get());
+  FTT_LAUNCH();
+  std::vector<float> hl(n);
+  FTT_CUDA(cudaMemcpyAsync(hl.data(), lam.get(), sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaStreamSynchronize(s));
+  // shifts moved apart by sep; clusters: runs of eigenvalues closer than ctol, whose
+  // inverse-iteration vectors are not independent enough to be used one by one
+  const float sep = (float)(16.0 * u32 * tnorm);
+  const double ctol = 128.0 * u32 * tnorm;
+  std::vector<float> hs(hl);
+  for (int i = 1; i < n; ++i)
+    if (hs[i] - hs[i - 1] < sep) hs[i] = hs[i - 1] + sep;
+  std::vector<int32_t> cb;   // cluster bounds: [cb[2q], cb[2q+1])
+  for (int i = 0; i < n;) {
+    int j = i + 1;
+    while (j < n && (double)hl[j] - (double)hl[j - 1] <= ctol) ++j;
+    if (j - i >= 2) {
+      cb.push_back(i);
+      cb.push_back(j);
+    }
+    i = j;
+  }
+  FTT_CUDA(cudaMemcpyAsync(shift.get(), hs.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  // 3. eigenvectors of T: inverse iteration, then subspace iteration on each cluster
+  DBuf<float> Z(nn, s);
+  {
+    DBuf<float> sdd(nn, s), sdu(nn, s), sdu2(nn, s), sdl(nn, s);
+    DBuf<unsigned char> spiv(nn, s);
+    const float pert = (float)(u32 * tnorm);
+    inverse_iteration_kernel<float><<<(unsigned)ceil_div(n, 32), 32, 0, s>>>(
+        d.get(), e.get(), n, shift.get(), 0, n, pert, sdd.get(), sdu.get(), sdu2.get(), sdl.get(), spiv.get(),
+        Z.get(), n);
+    FTT_LAUNCH();
+    if (!cb.empty()) {
+      DBuf<int32_t> dcb(cb.size(), s);
+      FTT_CUDA(cudaMemcpyAsync(dcb.get(), cb.data(), sizeof(int32_t) * cb.size(), cudaMemcpyHostToDevice, s));
+      cluster_orth_kernel<float><<<(unsigned)(cb.size() / 2), 256, 0, s>>>(dcb.get(), n, n, sdd.get(), sdu.get(),
+                                                                         sdu2.get(), sdl.get(), spiv.get(), Z.get(), n);
+      FTT_LAUNCH();
+      FTT_CUDA(cudaStreamSynchronize(s));   // cb is host memory read by the copy above
+    }
+  }
+  kclock_end(clk2, 0.0, s);
+  // 4. X = Q Z in FP64 storage with FP32-level products
+  DBuf<double> A64(nn, s), Z64(nn, s), tau64(n, s);
+  f32_to_f64_kernel<<<grid_for(nn), 256, 0, s>>>(A.get(), nn, A64.get());
+  FTT_LAUNCH();
+  f32_to_f64_kernel<<<grid_for(nn), 256, 0, s>>>(Z.get(), nn, Z64.get());
+  FTT_LAUNCH();
+  f32_to_f64_kernel<<<grid_for(n), 256, 0, s>>>(tau.get(), n, tau64.get());
+  FTT_LAUNCH();
+  A.reset();
+  Z.reset();
+  wy_back_transform(A64.get(), tau64.get(), n, Z64.get(), true, s);
+  transpose_f64(Z64.get(), n, n, V, s);   // V: row j = eigenvector j
+  lam_out.resize(n);
+  for (int i = 0; i < n; ++i) lam_out[i] = (double)hl[i] / sc;
   return true;
 }
 

@@ -65,7 +65,9 @@ class Stats(ctypes.Structure):
                 ("flop_gemm_tc", ctypes.c_double), ("sparse_bonds", ctypes.c_int64),
                 ("ms_tridiag", ctypes.c_double), ("flop_tridiag", ctypes.c_double), ("ms_tdeig", ctypes.c_double),
                 ("eig_tridiag", ctypes.c_int64), ("eig_fallbacks", ctypes.c_int64),
-                ("ms_gemm_oz", ctypes.c_double), ("flop_gemm_oz", ctypes.c_double)]
+                ("ms_gemm_oz", ctypes.c_double), ("flop_gemm_oz", ctypes.c_double),
+                ("ms_tridiag32", ctypes.c_double), ("flop_tridiag32", ctypes.c_double),
+                ("ms_tsqr", ctypes.c_double), ("flop_tsqr", ctypes.c_double), ("eig_fast", ctypes.c_int64)]
 
     def to_dict(self):
         d = self.d
@@ -85,7 +87,9 @@ class Stats(ctypes.Structure):
                 "sparse_bonds": self.sparse_bonds, "ms_tridiag": self.ms_tridiag,
                 "flop_tridiag": self.flop_tridiag, "ms_tdeig": self.ms_tdeig, "eig_tridiag": self.eig_tridiag,
                 "eig_fallbacks": self.eig_fallbacks, "ms_gemm_oz": self.ms_gemm_oz,
-                "flop_gemm_oz": self.flop_gemm_oz}
+                "flop_gemm_oz": self.flop_gemm_oz, "ms_tridiag32": self.ms_tridiag32,
+                "flop_tridiag32": self.flop_tridiag32, "ms_tsqr": self.ms_tsqr, "flop_tsqr": self.flop_tsqr,
+                "eig_fast": self.eig_fast}
 
 
 _P = ctypes.c_void_p
@@ -111,12 +115,15 @@ _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
 _lib.fasttt_debug_sym_eig.argtypes = [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, _P]
 _lib.fasttt_debug_gemm.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _P]
+_lib.fasttt_debug_gram.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, ctypes.c_int, _P]
+_lib.fasttt_debug_svd.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), _P, _P,
+                                  ctypes.c_int, _P]
 
 EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_tt_stats", "fasttt_tt_ranks",
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
            "tt_eval_backward_noalloc",
            "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig",
-           "fasttt_debug_gemm"]
+           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd"]
 
 
 class FastTTError(RuntimeError):
@@ -138,7 +145,7 @@ def debug_fail_alloc_after(n: int) -> None:
     _lib.fasttt_debug_fail_alloc_after(int(n))
 
 
-EIG_METHODS = {"tridiagonal": 0, "iterative": 1, "auto": 2}
+EIG_METHODS = {"tridiagonal": 0, "iterative": 1, "auto": 2, "fast": 3}
 
 
 def debug_sym_eig(G, method="auto", stream=None):
@@ -174,6 +181,37 @@ def debug_gemm(A, B, engine, stream=None):
     C = torch.empty((M, N), dtype=torch.float64, device=A.device)
     rc = _lib.fasttt_debug_gemm(M, N, K, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                 ctypes.c_void_p(C.data_ptr()), GEMM_TEST_ENGINES[engine], _stream(stream))
+    _check(rc)
+    return C
+
+
+def debug_svd(Z, precision="fp64", stream=None):
+    """Full SVD Z = U diag(sigma) Vt of an FP64 CUDA matrix through the library's rounding SVD
+    (a test hook).  Returns (sigma (r,) numpy descending, U (M, r) torch, Vt (r, N) torch)."""
+    _require_cuda()
+    Z = _dev(Z, torch.float64)
+    M, N = Z.shape
+    r = min(M, N)
+    U = torch.empty((M, r), dtype=torch.float64, device=Z.device)
+    Vt = torch.empty((r, N), dtype=torch.float64, device=Z.device)
+    sigma = np.zeros(r, dtype=np.float64)
+    if precision not in ("fp64", "mixed"):
+        raise FastTTError(EINVAL, "precision must be 'fp64' or 'mixed'")
+    prec = PREC_FP64 if precision == "fp64" else PREC_MIXED
+    rc = _lib.fasttt_debug_svd(M, N, ctypes.c_void_p(Z.data_ptr()), sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(Vt.data_ptr()), prec, _stream(stream))
+    _check(rc)
+    return sigma, U, Vt
+
+
+def debug_gram(A, engine, stream=None):
+    """C = A @ A.T for an FP64 CUDA matrix through the symmetric path of one GEMM kernel (a test hook)."""
+    _require_cuda()
+    A = _dev(A, torch.float64)
+    M, K = A.shape
+    C = torch.empty((M, M), dtype=torch.float64, device=A.device)
+    rc = _lib.fasttt_debug_gram(M, K, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                                GEMM_TEST_ENGINES[engine], _stream(stream))
     _check(rc)
     return C
 

@@ -71,7 +71,8 @@ def test_struct_layouts_match_header(lib):
     # fasttt_opts: six ints, two int64, two ints; fasttt_stats ends with the kernel-class doubles
     assert ctypes.sizeof(F.Opts) == 8 * 4 + 2 * 8
     assert F.Opts.sparse_sweep.offset == 6 * 4 + 2 * 8
-    assert F.Stats.flop_gemm_oz.offset + 8 == ctypes.sizeof(F.Stats)
+    assert F.Stats.flop_gemm_oz.offset + 8 == F.Stats.ms_tridiag32.offset
+    assert F.Stats.eig_fast.offset + 8 == ctypes.sizeof(F.Stats)
 
 
 def test_calls_without_gpu_fail_loudly(lib):

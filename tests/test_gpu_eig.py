@@ -96,3 +96,41 @@ def test_iterative_route(F):
 def test_eig_hook_rejects_bad_arguments(F):
     with pytest.raises(F.FastTTError):
         F.debug_sym_eig(torch.zeros((3, 4), dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("kind,n", [("separated", 300), ("separated", 1100), ("separated", 2500),
+                                    ("sparse_gram", 300), ("sparse_gram", 1100), ("sparse_gram", 2500),
+                                    ("clusters", 300)])
+def test_fast_route(F, kind, n):
+    """FP32 tridiagonal start + FP64-level refinement + Rayleigh-Ritz on close runs."""
+    _check(F, _matrix(kind, n, seed=53 + n), "fast")
+
+
+@pytest.mark.parametrize("kind,n", [("graded", 300), ("graded", 1100), ("rank_deficient", 300),
+                                    ("rank_deficient", 1100), ("clusters", 1100)])
+def test_fast_route_meets_the_bounds_or_declines(F, kind, n):
+    """Spectra with a large cluster below the FP32 start's resolution: the route may
+    decline (the library then takes the FP64 tridiagonal route), never answer wrongly."""
+    G = _matrix(kind, n, seed=57 + n)
+    try:
+        _check(F, G, "fast")
+    except F.FastTTError as e:
+        assert e.code == F.ENUMERIC, e
+
+
+def test_fast_route_near_clusters(F):
+    """Pairs of eigenvalues 1e-9 apart (below the FP32 start's resolution, above the
+    FP64 bound): the Rayleigh-Ritz step must separate them."""
+    rng = np.random.default_rng(59)
+    n = 600
+    base = np.linspace(1.0, 10.0, n // 2)
+    lam = np.sort(np.concatenate([base, base + 1e-9 * base]))
+    q = _orth(n, rng)
+    G = (q * lam) @ q.T
+    _check(F, 0.5 * (G + G.T), "fast")
+
+
+def test_fast_route_zero_matrix(F):
+    lam, V = F.debug_sym_eig(torch.zeros((50, 50), dtype=torch.float64, device="cuda"), method="fast")
+    assert np.all(lam == 0.0)
+    assert np.array_equal(V.cpu().numpy(), np.eye(50))

@@ -70,3 +70,47 @@ def test_fp32_level_engines(F, shape, engine):
 def test_dfma_engine(F):
     A, B = _mats(300, 200, 1000, seed=5)
     assert _err(F, A, B, "dfma") <= 4 * 1000 * U
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (300, 1000), (257, 4100), (1, 70), (1500, 3000)])
+@pytest.mark.parametrize("engine", ["tensor_f64", "dfma"])
+def test_gram_fp64_engines(F, shape, engine):
+    """C = A A^T through the symmetric path (upper tiles only; the tensor engine splits A once)."""
+    M, K = shape
+    A, _ = _mats(M, 1, K, seed=11 * M + K)
+    C = F.debug_gram(torch.from_numpy(A).cuda(), engine).cpu().numpy()
+    ref = A @ A.T
+    assert np.array_equal(C, C.T)
+    assert np.linalg.norm(C - ref) / np.linalg.norm(A) ** 2 <= 4 * K * U
+
+
+@pytest.mark.parametrize("engine", ["tensor_f32", "tf32x3"])
+def test_gram_fp32_level_engines(F, engine):
+    A, _ = _mats(400, 1, 2000, seed=17)
+    C = F.debug_gram(torch.from_numpy(A).cuda(), engine).cpu().numpy()
+    assert np.linalg.norm(C - A @ A.T) / np.linalg.norm(A) ** 2 <= 1e-6
+
+
+def test_tensor_core_fp64_engine_extreme_rows(F):
+    """Rows of zeros, subnormal rows, rows near the top of the exponent range and
+    subnormals inside normal rows: the slicing is exact integer work on the bits."""
+    rng = np.random.default_rng(23)
+    M, N, K = 200, 130, 300
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    A[3] = 0.0
+    A[5] *= 1e-310                                   # a whole row of subnormals
+    A[7] *= 1e300
+    A[9, ::7] = 4e-320                               # subnormals among normal entries
+    A[11] = rng.standard_normal(K) * 2.0 ** rng.integers(-1000, -960, size=K)
+    B[:, 2] = 0.0
+    B[:, 4] *= 1e-300
+    C = F.debug_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), "tensor_f64").cpu().numpy()
+    ref = A @ B
+    scale = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
+    scale[scale == 0] = 1.0
+    # the dropped bits are below 2^-56 of each row's (column's) maximum; subnormal
+    # inputs carry their own absolute rounding of 2^-1075
+    err = np.abs(C - ref) - 4.0 * K * 2.0 ** -1074 * (np.abs(B).max(axis=0)[None, :] + np.abs(A).max(axis=1)[:, None])
+    assert np.all(err <= 8 * U * scale)
+    assert np.all(C[3] == 0.0) and np.all(C[:, 2] == 0.0)
