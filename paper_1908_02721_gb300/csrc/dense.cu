@@ -953,7 +953,7 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
   if (!std::isfinite(g2)) return false;
   DBuf<double> R(nn, s), W(nn, s), S(nn, s), lam(n, s), Vbak(nn, s);
   const double u = mixed ? 0x1p-24 : 0x1p-53;
-  const double tiny = 64.0 * (double)n * u;
+  const double tiny = (mixed ? 64.0 : 1.0) * (double)n * u;
   constexpr double kGuard = 1.0 / 16.0;   // largest first-order correction applied
   double best = INFINITY;
   int since_best = 0;
@@ -980,7 +980,11 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
   for (int it = 0; it < 8; ++it) {
     const double err = evaluate(rF, offS);
     if (!std::isfinite(err)) return false;
-    if (rF <= tiny && offS <= tiny * gF) { best = err; since_best = 0; break; }   // converged
+    double lmax_it = 0.0;
+    for (double x : lam_out) lmax_it = std::max(lmax_it, fabs(x));
+    // converged: orthonormal and diagonal to the rounding level of n-term products
+    // (residuals ||G x_i - lambda_i x_i|| <= ||S - D||_F against ||G||_2)
+    if (rF <= tiny && offS <= tiny * lmax_it) { best = err; since_best = 0; break; }
     if (err < best) {
       best = err;
       since_best = 0;
@@ -1007,9 +1011,20 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
     evaluate(rF, offS);
     if (!(rF < 0.5)) return false;
   }
-  // Runs of close eigenvalues (ascending) whose residuals are not small against
-  // their gap: the eigenvector error is bounded by residual / gap, so neighbours
-  // with gap <= 16 max(residual) are resolved together by Rayleigh-Ritz.
+  // The refinement's separation threshold at the final state: pairs closer than it
+  // were never rotated apart by the first-order correction.
+  double delta_final;
+  {
+    double lmax = 0.0;
+    for (double x : lam_out) lmax = std::max(lmax, fabs(x));
+    const double s2 = std::min(offS, 2.0 * norm2_sym(S.get(), lam.get(), n, s));
+    const double r2 = std::min(rF, 2.0 * norm2_sym(R.get(), nullptr, n, s));
+    delta_final = 2.0 * (s2 + lmax * r2);
+  }
+  // Runs of close eigenvalues (ascending) that the refinement left mixed: closer
+  // than its threshold, or with residuals not small against their gap (the
+  // eigenvector error is bounded by residual / gap, the Rayleigh quotient's by
+  // residual^2 / gap).  Each run is resolved by Rayleigh-Ritz.
   std::vector<double> res(n);
   {
     offdiag_row_norms_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(S.get(), n, lam.get());
@@ -1028,7 +1043,7 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
   int64_t rr_work = 0;
   auto coupled = [&](int a, int b) {
     const double gap = lam_out[b] - lam_out[a], r = std::max(res[a], res[b]);
-    return gap <= 16.0 * r || r * r > ltol * gap;
+    return gap <= delta_final || gap <= 16.0 * r || r * r > ltol * gap;
   };
   for (int i = 0; i < n;) {
     int j = i + 1;
@@ -1039,6 +1054,9 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
     }
     i = j;
   }
+  // FP32-level refinement only needs the invariant subspaces (a run's vectors may stay
+  // mixed): Rayleigh-Ritz is an FP64 step
+  if (mixed) runs.clear();
   if (!runs.empty()) {
     if ((double)rr_work * (double)n > 4.0e11) return false;   // too much Jacobi work: another route
     DBuf<int32_t> dperm(n, s);
@@ -1067,14 +1085,15 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
       for (int64_t q = 0; q < c; ++q) lam_out[j0 + q] = sgn * h[q];
     }
   }
-  // Orthonormalise X to the rounding level of the products (Newton-Schulz).
-  for (int it = 0; it < 3; ++it) {
+  // Orthonormalise X to the rounding level of the products (Newton-Schulz,
+  // quadratic: one step takes ||I - X^T X|| from ~sqrt(n) u to the rounding floor).
+  for (int it = 0; it < 4; ++it) {
     gemm(mixed, n, n, n, 1.0, V, n, 1, V, 1, n, 0.0, R.get(), n, 1, s, true);
     i_minus_kernel<<<grid_for(nn), 256, 0, s>>>(R.get(), n);
     FTT_LAUNCH();
     const double rF = sqrt(sumsq(R.get(), nullptr, n, s));
     if (!(rF < 0.5)) return false;
-    if (rF <= 16.0 * (double)n * u) break;
+    if (rF <= 2.0 * (double)n * u) break;
     FTT_CUDA(cudaMemcpyAsync(S.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
     gemm(mixed, n, n, n, 0.5, R.get(), n, 1, S.get(), n, 1, 1.0, V, n, 1, s);
   }

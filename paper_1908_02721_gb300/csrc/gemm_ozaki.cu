@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tbase = tmem_base;
   const uint32_t idesc = idesc_bf16(kBM, kBN);
+  const uint64_t desc0 = sw64_desc(smem_u32(smem));
   // Exact integer accumulation of the level sums over K: the first kHiLevels levels
   // in hi (level g weighted 2^{BITS(kHiLevels+1-g)}), the rest in lo (weighted
   // 2^{BITS(S+1-g)}); a window adds below 2^{24+3 BITS} to each.
@@ -214,27 +215,29 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int w0 = 0; w0 < nk; w0 += kWindow) {
     const int w1 = (w0 + kWindow < nk) ? w0 + kWindow : nk;
     if (tid == 0 && !abort_flag) {
-      uint32_t started = 0;   // bit l: level l has a product in this window
       for (int kc = w0; kc < w1; ++kc) {
         const int st = kc & 1;
         if (!mbar_wait(&full_bar[st], tma_phase[st])) { abort_flag = 1; break; }
         tma_pending[st] = false;
         tma_phase[st] ^= 1;
         tc_fence_after();
-        const uint32_t a0 = smem_u32(smem + st * kStageBytes), b0 = a0 + S * kTileA;
-#pragma unroll 1
+        // descriptors: the address field is addr >> 4 in the low bits (no carry: shared
+        // memory addresses stay below 2^18), so tile and K offsets are plain additions
+        const uint64_t dst = desc0 + (uint64_t)((st * kStageBytes) >> 4);
+        const uint32_t first = (kc == w0) ? 0u : 1u;   // the window's first stage starts every level
+#pragma unroll
         for (int q = 1; q <= S; ++q) {
-          const uint64_t da = sw64_desc(a0 + (q - 1) * kTileA);
-#pragma unroll 1
+#pragma unroll
           for (int t = 1; t + q <= S + 1; ++t) {
             const int l = q + t - 2;
-            const uint64_t db = sw64_desc(b0 + (t - 1) * kTileB);
+            const uint64_t da = dst + (uint64_t)(((q - 1) * kTileA) >> 4);
+            const uint64_t db = dst + (uint64_t)((S * kTileA + (t - 1) * kTileB) >> 4);
+            // the first product of level l in the window is (q, t) = (1, l + 1) at K step 0
+            const uint32_t acc0 = (q == 1) ? first : 1u;
 #pragma unroll
-            for (int kk = 0; kk < kBKs / 16; ++kk) {   // K steps of 16 bf16 = 32 bytes
+            for (int kk = 0; kk < kBKs / 16; ++kk)   // K steps of 16 bf16 = 32 bytes
               umma_bf16(tbase + (uint32_t)(l * kBN), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
-                        (started >> l) & 1u);
-              started |= 1u << l;
-            }
+                        kk == 0 ? acc0 : 1u);
           }
         }
         umma_commit(&empty_bar[st]);

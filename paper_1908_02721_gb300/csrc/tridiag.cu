@@ -35,9 +35,15 @@ constexpr int kClusterMax = 256;   // largest eigenvalue cluster of the FP32 sta
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Householder tridiagonalisation (one cooperative launch).  Rows of the trailing
+// matrix are cut into up to kMaxSeg segments so that short rows still keep every
+// warp busy; a segment's partial product goes to part[segment][row] and the
+// partials are summed in a fixed order after the barrier (deterministic).
+constexpr int kMaxSeg = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-    tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* p, unsigned* bar) {
+    tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* part, unsigned* bar) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
   T* vs = reinterpret_cast<T*>(vs_raw);   // the current reflector v (v_0 = 1)
   T* ws = vs + n;                         // w = p - (tau/2)(p.v) v
@@ -46,6 +52,8 @@ __global__ void __launch_bounds__(256)
   unsigned gen = 0;
   for (int64_t k = 0; k + 2 < n; ++k) {
     const int64_t m = n - k - 1;
+    const int64_t nseg = max((int64_t)1, min((int64_t)kMaxSeg, W / m));
+    const int64_t seg = ((m + nseg - 1) / nseg + 31) / 32 * 32;   // segment length, a multiple of 32
     const T* x = A + k * n + k + 1;   // A[k, k+1:] = A[k+1:, k]
     T s = 0, z1 = 0, z2 = 0;
     for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) {
@@ -67,29 +75,35 @@ __global__ void __launch_bounds__(256)
       e[k] = beta;
       tau[k] = tk;
     }
-    // p = tau A22 v, one warp per row, four independent loads in flight per lane
-    for (int64_t i = gw; i < m; i += W) {
+    // partial products of A22 v: one warp per (row, segment), eight loads in flight per lane
+    for (int64_t task = gw; task < m * nseg; task += W) {
+      const int64_t i = task / nseg, sg = task % nseg;
       const T* row = A + (k + 1 + i) * n + (k + 1);
-      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      int64_t j = lane;
-      for (; j + 96 < m; j += 128) {
-        const T r0 = __ldcg(row + j), r1 = __ldcg(row + j + 32), r2 = __ldcg(row + j + 64), r3 = __ldcg(row + j + 96);
-        a0 = fma(r0, vs[j], a0);
-        a1 = fma(r1, vs[j + 32], a1);
-        a2 = fma(r2, vs[j + 64], a2);
-        a3 = fma(r3, vs[j + 96], a3);
+      const int64_t j0 = sg * seg, j1 = min(m, j0 + seg);
+      T a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = 0;
+      int64_t j = j0 + lane;
+      for (; j + 224 < j1; j += 256) {
+        T r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r[u] = __ldcg(row + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = fma(r[u], vs[j + 32 * u], a[u]);
       }
-      for (; j < m; j += 32) a0 = fma(__ldcg(row + j), vs[j], a0);
-      T acc = (a0 + a1) + (a2 + a3);
+      for (; j < j1; j += 32) a[0] = fma(__ldcg(row + j), vs[j], a[0]);
+      T acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) p[i] = tk * acc;
+      if (lane == 0) part[sg * n + i] = acc;
     }
     if (!grid_barrier(bar, gridDim.x, gen)) return;
     T pv = 0;
     z1 = z2 = 0;
     for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
-      const T pj = __ldcg(p + j);
+      T acc = 0;
+      for (int64_t sg = 0; sg < nseg; ++sg) acc += __ldcg(part + sg * n + j);
+      const T pj = tk * acc;
       ws[j] = pj;
       pv = fma(pj, vs[j], pv);
     }
@@ -98,18 +112,20 @@ __global__ void __launch_bounds__(256)
     for (int64_t j = threadIdx.x; j < m; j += blockDim.x) ws[j] = ws[j] - K * vs[j];
     __syncthreads();
     if (tk != T(0)) {
-      for (int64_t i = gw; i < m; i += W) {
+      for (int64_t task = gw; task < m * nseg; task += W) {
+        const int64_t i = task / nseg, sg = task % nseg;
         T* row = A + (k + 1 + i) * n + (k + 1);
         const T vi = vs[i], wi = ws[i];
-        int64_t j = lane;
-        for (; j + 96 < m; j += 128) {
-          const T r0 = __ldcg(row + j), r1 = __ldcg(row + j + 32), r2 = __ldcg(row + j + 64), r3 = __ldcg(row + j + 96);
-          row[j] = r0 - vi * ws[j] - wi * vs[j];
-          row[j + 32] = r1 - vi * ws[j + 32] - wi * vs[j + 32];
-          row[j + 64] = r2 - vi * ws[j + 64] - wi * vs[j + 64];
-          row[j + 96] = r3 - vi * ws[j + 96] - wi * vs[j + 96];
+        const int64_t j0 = sg * seg, j1 = min(m, j0 + seg);
+        int64_t j = j0 + lane;
+        for (; j + 224 < j1; j += 256) {
+          T r[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) r[u] = __ldcg(row + j + 32 * u);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) row[j + 32 * u] = r[u] - vi * ws[j + 32 * u] - wi * vs[j + 32 * u];
         }
-        for (; j < m; j += 32) row[j] = __ldcg(row + j) - vi * ws[j] - wi * vs[j];
+        for (; j < j1; j += 32) row[j] = __ldcg(row + j) - vi * ws[j] - wi * vs[j];
       }
     }
     if (blockIdx.x == 0)   // keep v in row k (columns k+1:) for the back-transformation
@@ -308,6 +324,7 @@ __global__ void __launch_bounds__(256) cluster_orth_kernel(const int32_t* c0, in
   __shared__ T red[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t a = c0[2 * blockIdx.x], b = c0[2 * blockIdx.x + 1];
+  if (a < 0 || b > n || b - a > kClusterMax) return;   // the host never sends such a cluster
   auto gram_schmidt = [&]() {
     for (int pass = 0; pass < 2; ++pass)
       for (int64_t k = a; k < b; ++k) {
@@ -509,7 +526,7 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   const size_t smem = 2 * sizeof(double) * (size_t)n;
   if (!coop || smem + 4096 > (size_t)smem_max) return false;
   const int64_t nn = (int64_t)n * n;
-  DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p(n, s);
+  DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)kMaxSeg * n, s);
   FTT_CUDA(cudaMemcpyAsync(A.get(), G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   // 1. tridiagonalisation
   {
@@ -648,7 +665,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     std::frexp(gmax, &eg);
     sc = std::ldexp(1.0, -eg);
   }
-  DBuf<float> A(nn, s), d(n, s), e(n, s), tau(n, s), p(n, s);
+  DBuf<float> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)kMaxSeg * n, s);
   scale_to_f32_kernel<<<grid_for(nn), 256, 0, s>>>(G, nn, sc, A.get());
   FTT_LAUNCH();
   // 1. FP32 tridiagonalisation
@@ -721,6 +738,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   for (int i = 0; i < n;) {
     int j = i + 1;
     while (j < n && (double)hl[j] - (double)hl[j - 1] <= ctol) ++j;
+    if (j - i > kClusterMax) return false;   // the cluster kernel holds kClusterMax columns
     if (j - i >= 2) {
       cb.push_back(i);
       cb.push_back(j);
