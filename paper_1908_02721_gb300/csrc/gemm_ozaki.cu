@@ -16,8 +16,8 @@
 // out of TMEM (tcgen05.ld) into 64-bit integer registers, packed four levels to an
 // integer, and the whole K reduction is exact.  FP64 enters only when the packed
 // sums are scaled into C.  FP64-level products: S = 8 slices of b = 7 bits
-// (levels below 2^{-63} dropped), windows of 256.  FP32-level products (mixed
-// precision): S = 3 slices of b = 8 bits, windows of 128.
+// (levels below 2^{-63} dropped), windows of 384.  FP32-level products (mixed
+// precision): S = 3 slices of b = 8 bits, windows of 192.
 //
 // Tiles: 128 (M) x 64 (N) per CTA; K in stages of 32 (64-byte bf16 rows) through
 // a two-deep shared-memory ring, the S slices of A and of B of a stage loaded by
@@ -30,10 +30,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "dense.cuh"
 
@@ -74,12 +72,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
+// Contiguous bulk copy global -> shared (size a multiple of 16 bytes, both 16-byte aligned).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 // K-major operand tile of rows x 32 bf16 (64-byte rows), 64-byte swizzle: 8-row
@@ -114,6 +112,19 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread), one wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -147,7 +158,7 @@ __host__ __device__ constexpr long long oz_level_max() {
 // into 64-bit integers (KD times the largest level sum per k stays below 2^24).
 template <int S, int BITS, int KD>
 __global__ void __launch_bounds__(kThreads, 1)
-    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t M,
+    ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ qa, const __nv_bfloat16* __restrict__ qb, int64_t M,
                       int64_t N, int64_t Kp, int64_t Mp, int64_t Np, const int* __restrict__ ea,
                       const int* __restrict__ fb, double alpha, double beta, double* __restrict__ C, int64_t sci,
                       int64_t scj, bool sym) {
@@ -200,9 +211,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto load_stage = [&](int st, int kc) {
     unsigned char* base = smem + st * kStageBytes;
     mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
+    // tile images: [slice][k block][64-row tile] of 4 KB (see oz_slice_kernel); the A
+    // tile is two consecutive 64-row images, the B tile one
+    const int64_t nkb = Kp / kBKs;
     for (int q = 0; q < S; ++q) {
-      tma_load_2d(base + q * kTileA, &tmA, &full_bar[st], kc * kBKs, (int)(q * Mp + (int64_t)bm * kBM));
-      tma_load_2d(base + S * kTileA + q * kTileB, &tmB, &full_bar[st], kc * kBKs, (int)(q * Np + (int64_t)bn * kBN));
+      bulk_load(base + q * kTileA, qa + (((int64_t)q * nkb + kc) * (Mp / 64) + (int64_t)bm * 2) * 2048, kTileA,
+                &full_bar[st]);
+      bulk_load(base + S * kTileA + q * kTileB, qb + (((int64_t)q * nkb + kc) * (Np / 64) + bn) * 2048, kTileB,
+                &full_bar[st]);
     }
   };
   // issuing thread's view of the copies in flight (for a clean exit after a timeout)
@@ -258,21 +274,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     // drain: TMEM lanes 32 * quarter .. (tile rows), columns 32 * half .. of every level
     const uint32_t lane_base = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
 #pragma unroll
-    for (int l = 0; l < kLevels; ++l)
+    for (int l = 0; l < kLevels; ++l) {
+      uint32_t r[32];
+      tmem_ld32(lane_base + (uint32_t)(l * kBN), r);
+      if (l < kHiLevels) {
+        const int sh = BITS * (kHiLevels - 1 - l);
 #pragma unroll
-      for (int c0 = 0; c0 < 32; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(lane_base + (uint32_t)(l * kBN + c0), r);
-        if (l < kHiLevels) {
-          const int sh = BITS * (kHiLevels - 1 - l);
+        for (int c = 0; c < 32; ++c) hi[c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
+      } else {
+        const int sh = BITS * (kLevels - 1 - l);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) hi[c0 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
-        } else {
-          const int sh = BITS * (kLevels - 1 - l);
-#pragma unroll
-          for (int c = 0; c < 16; ++c) lo[c0 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
-        }
+        for (int c = 0; c < 32; ++c) lo[c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
       }
+    }
     tc_fence_before();
     __syncthreads();
   }
@@ -425,16 +439,25 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
       if (c0 == 0 && i < rows) ex[i] = e;
     }
     __syncthreads();
+    // Stored as the shared-memory images the GEMM's UMMA descriptors read: per slice,
+    // per k block of 32 and per 64-row tile a 4 KB block of 64-byte rows (32 bf16), its
+    // 16-byte chunk c of row r at position c ^ ((r >> 1) & 3) (the 64-byte swizzle).
+    // Lanes 0-15 write k block c0/32 of the row, lanes 16-31 the next one.
+    const int64_t nkb = cols_p / 32, nrt = rows_p / 64;
+    const int kbl = lane >> 4, kk = 2 * (lane & 15), ch = kk >> 3, el = kk & 7;
 #pragma unroll 1
     for (int rr = warp * 8; rr < warp * 8 + 8; ++rr) {
       const int e = es[rr];
       int d0[S], d1[S];
       oz_digits<S, BITS>(t[rr][2 * lane], e, d0);
       oz_digits<S, BITS>(t[rr][2 * lane + 1], e, d1);
-      const int64_t base = ((r0 + rr) * cols_p + c0) / 2 + lane;
+      const int64_t row = r0 + rr, kb = c0 / 32 + kbl;
+      const int r = (int)(row & 63);
+      const int64_t within = (int64_t)r * 16 + ((ch ^ ((r >> 1) & 3)) * 4) + (el >> 1);   // in 4-byte words
 #pragma unroll
       for (int sl = 0; sl < S; ++sl)
-        q32[(int64_t)sl * (rows_p * cols_p / 2) + base] = oz_bf16_bits(d0[sl]) | (oz_bf16_bits(d1[sl]) << 16);
+        q32[(((int64_t)sl * nkb + kb) * nrt + (row >> 6)) * 1024 + within] =
+            oz_bf16_bits(d0[sl]) | (oz_bf16_bits(d1[sl]) << 16);
     }
     __syncthreads();
   }
@@ -465,33 +488,6 @@ __global__ void mirror_upper_oz_kernel(double* C, int64_t n) {
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols_p, int box_rows) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)cols_p, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols_p * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kBKs, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int S, int BITS, int KD>
 bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
                const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
@@ -517,13 +513,12 @@ bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
   // A itself (a Gram product) its slices are A's, padded to Mp >= Np rows.
   oz_split<S, BITS>(A, M, K, sai, sak, Mp, Kp, ea.get(), qa.get(), s);
   if (!same) oz_split<S, BITS>(B, N, K, sbj, sbk, Np, Kp, fb.get(), qb.get(), s);
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, qa.get(), S * Mp, Kp, kBM)) return false;
-  if (same ? !make_map(&mb, qa.get(), S * Mp, Kp, kBN) : !make_map(&mb, qb.get(), S * Np, Kp, kBN)) return false;
+
   KClock clk;
   kclock_begin(clk, KC_GEMM_OZ, s);
   ozaki_gemm_kernel<S, BITS, KD><<<dim3((unsigned)(Mp / kBM), (unsigned)(Np / kBN)), kThreads, smem, s>>>(
-      ma, mb, M, N, Kp, Mp, same ? Mp : Np, ea.get(), same ? ea.get() : fb.get(), alpha, beta, C, sci, scj, sym);
+      qa.get(), same ? qa.get() : qb.get(), M, N, Kp, Mp, same ? Mp : Np, ea.get(), same ? ea.get() : fb.get(), alpha,
+      beta, C, sci, scj, sym);
   FTT_LAUNCH();
   kclock_end(clk, (sym ? 1.0 : 2.0) * (double)M * (double)N * (double)K, s);
   if (sym) {
@@ -553,10 +548,10 @@ bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const
   if (M <= 0 || N <= 0) return true;
   if (sym && (M != N || sci != N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
   if (K <= 0) return false;
-  // FP64 level: 8 slices of 7 bits (level sums exact over windows of 256);
-  // FP32 level: 3 slices of 8 bits (windows of 128)
-  if (slices == 7) return run_ozaki<8, 7, 256>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
-  if (slices == 3) return run_ozaki<3, 8, 128>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  // FP64 level: 8 slices of 7 bits (level sums exact over windows of 384: 384 x 40960 < 2^24);
+  // FP32 level: 3 slices of 8 bits (windows of 192: 192 x 81920 < 2^24)
+  if (slices == 7) return run_ozaki<8, 7, 384>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  if (slices == 3) return run_ozaki<3, 8, 192>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
   return false;
 }
 
