@@ -9,6 +9,9 @@
 // read from the warp's stored left partials (recompute = 0: sum_k r_k values per
 // warp) or recomputed from G_1..G_{k-1} (recompute = 1: 2 r_max values per warp).
 // Updates are atomic adds into the caller's gradient cores.
+//
+// Small TTs (d <= 8, every rank <= 8) are evaluated with one thread per entry and
+// the partial product in registers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -159,6 +162,51 @@ __global__ void __launch_bounds__(kMaxWarps * 32) backward_kernel(int d, CoreArg
   }
 }
 
+// ---- small TTs (d <= kSmallD, every rank <= kSmallR): entry evaluation with one
+// thread per entry and the running row vector in registers.
+constexpr int kSmallD = 8, kSmallR = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) small_eval_kernel(int d, CoreArgs ca, int64_t m, const int32_t* __restrict__ idx,
+                                                         T* __restrict__ out, unsigned* err) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    T v[kSmallR], w[kSmallR];
+    v[0] = 1;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < kSmallD; ++k) {
+      if (k < d) {
+        int32_t i = __ldg(idx + (int64_t)k * m + e);
+        const int r0 = ca.r[k], r1 = ca.r[k + 1], n = ca.n[k];
+        if (i < 0 || i >= n) { bad = true; i = 0; }
+        const T* G = (const T*)ca.core[k] + (int64_t)i * r1;
+#pragma unroll
+        for (int b = 0; b < kSmallR; ++b) w[b] = 0;
+#pragma unroll
+        for (int a = 0; a < kSmallR; ++a) {
+          if (a < r0) {
+            const T* row = G + (int64_t)a * n * r1;
+#pragma unroll
+            for (int b = 0; b < kSmallR; ++b)
+              if (b < r1) w[b] = fma(v[a], __ldg(row + b), w[b]);
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < kSmallR; ++b) v[b] = w[b];
+      }
+    }
+    if (bad) { atomicOr(err, 1u); out[e] = 0; }
+    else out[e] = v[0];
+  }
+}
+
+bool small_shape(const CoreArgs& ca, int d) {
+  if (d > kSmallD) return false;
+  for (int k = 0; k <= d; ++k)
+    if (ca.r[k] > kSmallR) return false;
+  return true;
+}
+
 // warps per block so that `vecs` vectors of rmax values per warp fit the budget
 template <typename K>
 int warps_for(K kernel, int64_t rmax, int vecs, size_t esz, size_t* smem) {
@@ -211,7 +259,13 @@ int tt_eval_at_impl(int d, const int64_t* dims, const int64_t* ranks, const void
   FTT_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(unsigned), s));
   const int rmax = max_rank_of(ca, d);
   size_t smem = 0;
-  if (dtype == FASTTT_F64) {
+  if (small_shape(ca, d)) {
+    const int64_t blocks = std::min<int64_t>(ceil_div(m, 256), (int64_t)kNumSMs * 8);
+    if (dtype == FASTTT_F64)
+      small_eval_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(d, ca, m, idx, (double*)out, err.get());
+    else
+      small_eval_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(d, ca, m, idx, (float*)out, err.get());
+  } else if (dtype == FASTTT_F64) {
     const int nw = warps_for(eval_kernel<double>, rmax, 2, 8, &smem);
     const int64_t blocks = std::min<int64_t>(ceil_div(m, nw), (int64_t)kNumSMs * 16);
     eval_kernel<double><<<(unsigned)blocks, nw * 32, smem, s>>>(d, ca, m, idx, (double*)out, err.get(), rmax);
