@@ -82,7 +82,7 @@ typedef struct fasttt_opts {
 /* Engine of the dense FP64 contractions.  TENSOR: products of at least 2^26
  * multiply-adds run on the tcgen05 tensor cores from exact bf16 slices of the
  * FP64 operands (8 slices of 7 bits: every slice product exact, the level sums
- * exact in FP32 over windows of 256 and then in 64-bit integers; FP64-level
+ * exact in FP32 over windows of 384 and then in 64-bit integers; FP64-level
  * results, Ozaki-Ogita-Oishi-Rump splitting), smaller ones on FP64 DFMA.  DFMA:
  * every FP64 product on FP64 DFMA.  In mixed precision, TENSOR runs the large
  * products from 3 slices of 8 bits (FP32-level).  A tensor-core kernel whose

@@ -55,20 +55,20 @@ __global__ void __launch_bounds__(256)
     const int64_t nseg = max((int64_t)1, min((int64_t)kMaxSeg, W / m));
     const int64_t seg = ((m + nseg - 1) / nseg + 31) / 32 * 32;   // segment length, a multiple of 32
     const T* x = A + k * n + k + 1;   // A[k, k+1:] = A[k+1:, k]
+    // row k into shared memory in one pass of independent loads, then the norm from there
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = __ldcg(x + j);
+    __syncthreads();
     T s = 0, z1 = 0, z2 = 0;
-    for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) {
-      const T t = __ldcg(x + j);
-      s = fma(t, t, s);
-    }
-    block_sum3<T>(s, z1, z2);
-    const T alpha = __ldcg(x);
+    for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) s = fma(vs[j], vs[j], s);
+    block_sum3<T>(s, z1, z2);   // ends with a barrier
+    const T alpha = vs[0];
     T beta = alpha, tk = 0, scale = 0;
     if (s > T(0)) {
       beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
       tk = (beta - alpha) / beta;
       scale = T(1) / (alpha - beta);
     }
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = (j == 0) ? T(1) : __ldcg(x + j) * scale;
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = (j == 0) ? T(1) : vs[j] * scale;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       d[k] = __ldcg(A + k * n + k);
