@@ -990,7 +990,7 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
       since_best = 0;
       FTT_CUDA(cudaMemcpyAsync(Vbak.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
       have_bak = true;
-    } else if (++since_best >= 2) {
+    } else if (++since_best >= 2 && it >= 4) {   // well-separated pairs converge within four steps
       break;
     }
     if (!(rF < 0.5) || it == 7) break;   // the state of the last evaluation is kept
@@ -1048,7 +1048,11 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
   for (int i = 0; i < n;) {
     int j = i + 1;
     while (j < n && coupled(perm[j - 1], perm[j])) ++j;
-    if (j - i >= 2 && lam_out[perm[j - 1]] - lam_out[perm[i]] > wtol) {
+    // a run whose Rayleigh quotients agree to rounding is a multiple eigenvalue only if its
+    // residuals are at rounding level too (a pair mixed at 45 degrees has equal quotients)
+    double rmax = 0.0;
+    for (int q = i; q < j; ++q) rmax = std::max(rmax, res[perm[q]]);
+    if (j - i >= 2 && (lam_out[perm[j - 1]] - lam_out[perm[i]] > wtol || rmax > ltol)) {
       runs.emplace_back(i, j);
       rr_work += (int64_t)(j - i) * (j - i);
     }

@@ -35,51 +35,92 @@ constexpr int kClusterMax = 256;   // largest eigenvalue cluster of the FP32 sta
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Householder tridiagonalisation (one cooperative launch).  Rows of the trailing
-// matrix are cut into up to kMaxSeg segments so that short rows still keep every
-// warp busy; a segment's partial product goes to part[segment][row] and the
-// partials are summed in a fixed order after the barrier (deterministic).
+// Householder tridiagonalisation (one cooperative launch), one grid barrier per
+// column.  Warps own rows (or row segments) of the trailing matrix; in the pass
+// of column k a warp applies column k-1's rank-2 update A -= v w^T + w v^T to
+// its rows and takes their dot products with reflector k in the same sweep.
+// Reflector k comes from row k after column k-1's update, which every block forms
+// redundantly in shared memory (no one writes it in global memory), so the only
+// grid-wide dependency left is p = tau A v.  Rows are cut into up to kMaxSeg
+// segments so that short rows still keep every warp busy; a segment's partial
+// product goes to part[segment][row] and the partials are summed in a fixed
+// order after the barrier (deterministic).  Row k keeps v_k (v_0 = 1 stored),
+// written once every block has formed its copy of row k (after the barrier).
 constexpr int kMaxSeg = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256)
     tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* part, unsigned* bar) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
-  T* vs = reinterpret_cast<T*>(vs_raw);   // the current reflector v (v_0 = 1)
-  T* ws = vs + n;                         // w = p - (tau/2)(p.v) v
+  T* vs = reinterpret_cast<T*>(vs_raw);   // v_k
+  T* vp = vs + n;                         // v_{k-1}
+  T* ws = vp + n;                         // w_{k-1} = p - (tau/2)(p.v) v
+  T* rk = ws + n;                         // row k after column k-1's update
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + warp, W = (int64_t)gridDim.x * 8;
   unsigned gen = 0;
+  T tprev = 0;   // tau_{k-1}
+  int64_t nseg_prev = 1;
+  // w of the previous column from its partials (trailing size mp)
+  // partials of column k live in part[(k & 1) * kMaxSeg * n ..]: a block may write column
+  // k+1's while another still reads column k's (both between the same two barriers)
+  auto form_w = [&](int64_t mp, int64_t kprev) {
+    const T* pp = part + (kprev & 1) * kMaxSeg * n;
+    T pv = 0, z1 = 0, z2 = 0;
+    for (int64_t j = threadIdx.x; j < mp; j += blockDim.x) {
+      T acc = 0;
+      for (int64_t sg = 0; sg < nseg_prev; ++sg) acc += __ldcg(pp + sg * n + j);
+      ws[j] = acc;   // tau already applied
+      pv = fma(acc, vp[j], pv);
+    }
+    block_sum3<T>(pv, z1, z2);   // ends with a barrier
+    const T K = T(0.5) * tprev * pv;
+    for (int64_t j = threadIdx.x; j < mp; j += blockDim.x) ws[j] = ws[j] - K * vp[j];
+    __syncthreads();
+  };
   for (int64_t k = 0; k + 2 < n; ++k) {
     const int64_t m = n - k - 1;
-    const int64_t nseg = max((int64_t)1, min((int64_t)kMaxSeg, W / m));
-    const int64_t seg = ((m + nseg - 1) / nseg + 31) / 32 * 32;   // segment length, a multiple of 32
-    const T* x = A + k * n + k + 1;   // A[k, k+1:] = A[k+1:, k]
-    // row k into shared memory in one pass of independent loads, then the norm from there
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = __ldcg(x + j);
+    const bool upd = (k > 0) && (tprev != T(0));   // column k-1's update is not the identity
+    if (k > 0) {
+      form_w(m + 1, k - 1);
+      // every block has read row k-1 (before the last barrier): keep v_{k-1} there now
+      if (blockIdx.x == 0)
+        for (int64_t j = threadIdx.x; j < m + 1; j += blockDim.x) A[(k - 1) * n + k + j] = vp[j];
+    }
+    // row k after column k-1's update (index 0 of that trailing matrix)
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+      T x = __ldcg(A + k * n + k + 1 + j);
+      if (upd) x = x - vp[0] * ws[1 + j] - ws[0] * vp[1 + j];
+      rk[j] = x;
+    }
     __syncthreads();
     T s = 0, z1 = 0, z2 = 0;
-    for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) s = fma(vs[j], vs[j], s);
+    for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) s = fma(rk[j], rk[j], s);
     block_sum3<T>(s, z1, z2);   // ends with a barrier
-    const T alpha = vs[0];
+    const T alpha = rk[0];
     T beta = alpha, tk = 0, scale = 0;
     if (s > T(0)) {
       beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
       tk = (beta - alpha) / beta;
       scale = T(1) / (alpha - beta);
     }
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = (j == 0) ? T(1) : vs[j] * scale;
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) vs[j] = (j == 0) ? T(1) : rk[j] * scale;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      d[k] = __ldcg(A + k * n + k);
+      T dk = __ldcg(A + k * n + k);
+      if (upd) dk = dk - T(2) * vp[0] * ws[0];
+      d[k] = dk;
       e[k] = beta;
       tau[k] = tk;
     }
-    // partial products of A22 v: one warp per (row, segment), eight loads in flight per lane
+    // fused pass: rows k+1+i (i < m), columns k+1+j (j < m) of the column-k trailing matrix
+    const int64_t nseg = max((int64_t)1, min((int64_t)kMaxSeg, W / m));
+    const int64_t seg = ((m + nseg - 1) / nseg + 31) / 32 * 32;   // segment length, a multiple of 32
     for (int64_t task = gw; task < m * nseg; task += W) {
       const int64_t i = task / nseg, sg = task % nseg;
-      const T* row = A + (k + 1 + i) * n + (k + 1);
+      T* row = A + (k + 1 + i) * n + (k + 1);
       const int64_t j0 = sg * seg, j1 = min(m, j0 + seg);
+      const T vi = upd ? vp[1 + i] : T(0), wi = upd ? ws[1 + i] : T(0);
       T a[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) a[u] = 0;
@@ -88,57 +129,58 @@ __global__ void __launch_bounds__(256)
         T r[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) r[u] = __ldcg(row + j + 32 * u);
+        if (upd) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            r[u] = r[u] - vi * ws[1 + j + 32 * u] - wi * vp[1 + j + 32 * u];
+            row[j + 32 * u] = r[u];
+          }
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) a[u] = fma(r[u], vs[j + 32 * u], a[u]);
       }
-      for (; j < j1; j += 32) a[0] = fma(__ldcg(row + j), vs[j], a[0]);
+      for (; j < j1; j += 32) {
+        T r = __ldcg(row + j);
+        if (upd) {
+          r = r - vi * ws[1 + j] - wi * vp[1 + j];
+          row[j] = r;
+        }
+        a[0] = fma(r, vs[j], a[0]);
+      }
       T acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) part[sg * n + i] = acc;
+      if (lane == 0) part[(k & 1) * kMaxSeg * n + sg * n + i] = tk * acc;
     }
     if (!grid_barrier(bar, gridDim.x, gen)) return;
-    T pv = 0;
-    z1 = z2 = 0;
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
-      T acc = 0;
-      for (int64_t sg = 0; sg < nseg; ++sg) acc += __ldcg(part + sg * n + j);
-      const T pj = tk * acc;
-      ws[j] = pj;
-      pv = fma(pj, vs[j], pv);
-    }
-    block_sum3<T>(pv, z1, z2);   // ends with a barrier: ws holds p
-    const T K = T(0.5) * tk * pv;
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) ws[j] = ws[j] - K * vs[j];
-    __syncthreads();
-    if (tk != T(0)) {
-      for (int64_t task = gw; task < m * nseg; task += W) {
-        const int64_t i = task / nseg, sg = task % nseg;
-        T* row = A + (k + 1 + i) * n + (k + 1);
-        const T vi = vs[i], wi = ws[i];
-        const int64_t j0 = sg * seg, j1 = min(m, j0 + seg);
-        int64_t j = j0 + lane;
-        for (; j + 224 < j1; j += 256) {
-          T r[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) r[u] = __ldcg(row + j + 32 * u);
-#pragma unroll
-          for (int u = 0; u < 8; ++u) row[j + 32 * u] = r[u] - vi * ws[j + 32 * u] - wi * vs[j + 32 * u];
-        }
-        for (; j < j1; j += 32) row[j] = __ldcg(row + j) - vi * ws[j] - wi * vs[j];
-      }
-    }
-    if (blockIdx.x == 0)   // keep v in row k (columns k+1:) for the back-transformation
-      for (int64_t j = threadIdx.x; j < m; j += blockDim.x) A[k * n + k + 1 + j] = vs[j];
-    if (!grid_barrier(bar, gridDim.x, gen)) return;
+    // v_k becomes the previous reflector
+    T* t = vp; vp = vs; vs = t;
+    tprev = tk;
+    nseg_prev = nseg;
+  }
+  // the last 2 x 2 block after the last column's update; v of the last column into its row
+  if (n >= 3) {
+    form_w(2, n - 3);
+    if (blockIdx.x == 0)
+      for (int64_t j = threadIdx.x; j < 2; j += blockDim.x) A[(n - 3) * n + n - 2 + j] = vp[j];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (n >= 2) {
-      d[n - 2] = __ldcg(A + (n - 2) * n + n - 2);
-      e[n - 2] = __ldcg(A + (n - 2) * n + n - 1);
+      const bool upd = (n >= 3) && (tprev != T(0));
+      T a00 = __ldcg(A + (n - 2) * n + n - 2), a01 = __ldcg(A + (n - 2) * n + n - 1),
+        a11 = __ldcg(A + (n - 1) * n + n - 1);
+      if (upd) {
+        a00 = a00 - T(2) * vp[0] * ws[0];
+        a01 = a01 - vp[0] * ws[1] - ws[0] * vp[1];
+        a11 = a11 - T(2) * vp[1] * ws[1];
+      }
+      d[n - 2] = a00;
+      e[n - 2] = a01;
       tau[n - 2] = T(0);
+      d[n - 1] = a11;
+    } else {
+      d[n - 1] = __ldcg(A + (n - 1) * n + n - 1);
     }
-    d[n - 1] = __ldcg(A + (n - 1) * n + n - 1);
   }
 }
 
@@ -523,10 +565,10 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = 2 * sizeof(double) * (size_t)n;
+  const size_t smem = 4 * sizeof(double) * (size_t)n;
   if (!coop || smem + 4096 > (size_t)smem_max) return false;
   const int64_t nn = (int64_t)n * n;
-  DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)kMaxSeg * n, s);
+  DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)2 * kMaxSeg * n, s);
   FTT_CUDA(cudaMemcpyAsync(A.get(), G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   // 1. tridiagonalisation
   {
@@ -641,7 +683,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = 2 * sizeof(float) * (size_t)n;
+  const size_t smem = 4 * sizeof(float) * (size_t)n;
   const int64_t nn = (int64_t)n * n;
   // every vector's tridiagonal factors are kept for the cluster iterations: 17 n^2 bytes
   if (!coop || smem + 4096 > (size_t)smem_max || 17.0 * (double)nn > 6.0e9) return false;
@@ -665,7 +707,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     std::frexp(gmax, &eg);
     sc = std::ldexp(1.0, -eg);
   }
-  DBuf<float> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)kMaxSeg * n, s);
+  DBuf<float> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)2 * kMaxSeg * n, s);
   scale_to_f32_kernel<<<grid_for(nn), 256, 0, s>>>(G, nn, sc, A.get());
   FTT_LAUNCH();
   // 1. FP32 tridiagonalisation
