@@ -156,7 +156,7 @@ __host__ __device__ constexpr long long oz_level_max() {
 // in stages of 32 through a two-deep shared-memory ring (TMA, SWIZZLE_64B); the
 // level sums accumulate in TMEM over windows of KD and are then drained exactly
 // into 64-bit integers (KD times the largest level sum per k stays below 2^24).
-template <int S, int BITS, int KD>
+template <int S, int BITS, int KD, int BN, int NST>
 __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ qa, const __nv_bfloat16* __restrict__ qb, int64_t M,
                       int64_t N, int64_t Kp, int64_t Mp, int64_t Np, const int* __restrict__ ea,
@@ -164,21 +164,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                       int64_t scj, bool sym) {
   static_assert((long long)KD * oz_level_max<S, BITS>() < (1ll << 24), "level sums of a window must stay exact");
   static_assert(KD % kBKs == 0, "windows are whole stages");
+  static_assert(S * BN <= 512 && BN % 64 == 0, "the level accumulators must fit TMEM");
   constexpr int kLevels = S;                       // g = 2 .. S + 1
-  constexpr uint32_t kCols = (kLevels * kBN <= 256) ? 256 : 512;
-  constexpr uint32_t kTileA = kBM * kBKs * 2, kTileB = kBN * kBKs * 2;
+  constexpr uint32_t kCols = (kLevels * BN <= 256) ? 256 : 512;
+  constexpr uint32_t kTileA = kBM * kBKs * 2, kTileB = BN * kBKs * 2;
   constexpr uint32_t kStageBytes = S * (kTileA + kTileB);
   constexpr int kWindow = KD / kBKs;
+  constexpr int kCPT = BN / 2;                     // columns per thread in the drain
   const int bm = blockIdx.x, bn = blockIdx.y;
-  if (sym && (int64_t)bm * kBM >= (int64_t)(bn + 1) * kBN) return;   // strictly below the diagonal
+  if (sym && (int64_t)bm * kBM >= (int64_t)(bn + 1) * BN) return;   // strictly below the diagonal
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full_bar[2], empty_bar[2], drain_bar;
+  __shared__ uint64_t full_bar[NST], empty_bar[NST], drain_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NST; ++q) {
       mbar_init(&full_bar[q], 1);
       mbar_init(&empty_bar[q], 1);
     }
@@ -196,43 +198,48 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t idesc = idesc_bf16(kBM, kBN);
+  const uint32_t idesc = idesc_bf16(kBM, BN);
   const uint64_t desc0 = sw64_desc(smem_u32(smem));
   // Exact integer accumulation of the level sums over K: the first kHiLevels levels
   // in hi (level g weighted 2^{BITS(kHiLevels+1-g)}), the rest in lo (weighted
   // 2^{BITS(S+1-g)}); a window adds below 2^{24+3 BITS} to each.
   constexpr int kHiLevels = (S < 4) ? S : 4;
   constexpr int kLoLevels = S - kHiLevels;
-  long long hi[32], lo[32];
+  constexpr int kLoN = (kLoLevels > 0) ? kCPT : 1;
+  long long hi[kCPT], lo[kLoN];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0;
+  for (int c = 0; c < kCPT; ++c) hi[c] = 0;
+#pragma unroll
+  for (int c = 0; c < kLoN; ++c) lo[c] = 0;
   const int nk = (int)(Kp / kBKs);
   const int quarter = warp & 3, half = warp >> 2;
   auto load_stage = [&](int st, int kc) {
     unsigned char* base = smem + st * kStageBytes;
     mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
     // tile images: [slice][k block][64-row tile] of 4 KB (see oz_slice_kernel); the A
-    // tile is two consecutive 64-row images, the B tile one
+    // tile is two consecutive 64-row images, the B tile BN / 64
     const int64_t nkb = Kp / kBKs;
     for (int q = 0; q < S; ++q) {
       bulk_load(base + q * kTileA, qa + (((int64_t)q * nkb + kc) * (Mp / 64) + (int64_t)bm * 2) * 2048, kTileA,
                 &full_bar[st]);
-      bulk_load(base + S * kTileA + q * kTileB, qb + (((int64_t)q * nkb + kc) * (Np / 64) + bn) * 2048, kTileB,
-                &full_bar[st]);
+      bulk_load(base + S * kTileA + q * kTileB,
+                qb + (((int64_t)q * nkb + kc) * (Np / 64) + (int64_t)bn * (BN / 64)) * 2048, kTileB, &full_bar[st]);
     }
   };
   // issuing thread's view of the copies in flight (for a clean exit after a timeout)
-  bool tma_pending[2] = {false, false};
-  uint32_t tma_phase[2] = {0, 0};
+  bool tma_pending[NST];
+  uint32_t tma_phase[NST], empty_phase[NST];
+#pragma unroll
+  for (int q = 0; q < NST; ++q) { tma_pending[q] = false; tma_phase[q] = 0; empty_phase[q] = 0; }
   if (tid == 0)
-    for (int st = 0; st < 2 && st < nk; ++st) { load_stage(st, st); tma_pending[st] = true; }
+    for (int st = 0; st < NST && st < nk; ++st) { load_stage(st, st); tma_pending[st] = true; }
   bool ok = true;
   uint32_t drain_phase = 0;
   for (int w0 = 0; w0 < nk; w0 += kWindow) {
     const int w1 = (w0 + kWindow < nk) ? w0 + kWindow : nk;
     if (tid == 0 && !abort_flag) {
       for (int kc = w0; kc < w1; ++kc) {
-        const int st = kc & 1;
+        const int st = kc % NST;
         if (!mbar_wait(&full_bar[st], tma_phase[st])) { abort_flag = 1; break; }
         tma_pending[st] = false;
         tma_phase[st] ^= 1;
@@ -252,16 +259,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t acc0 = (q == 1) ? first : 1u;
 #pragma unroll
             for (int kk = 0; kk < kBKs / 16; ++kk)   // K steps of 16 bf16 = 32 bytes
-              umma_bf16(tbase + (uint32_t)(l * kBN), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
+              umma_bf16(tbase + (uint32_t)(l * BN), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
                         kk == 0 ? acc0 : 1u);
           }
         }
         umma_commit(&empty_bar[st]);
-        // refill the other stage (consumed by step kc - 1) with step kc + 1
-        if (kc >= 1 && kc + 1 < nk) {
-          const int o = st ^ 1;
-          if (!mbar_wait(&empty_bar[o], (uint32_t)(((kc - 1) >> 1) & 1))) { abort_flag = 1; break; }
-          load_stage(o, kc + 1);
+        // refill the stage of step kc - 1 (its MMAs run ahead of these) with step kc - 1 + NST
+        if (kc >= 1 && kc - 1 + NST < nk) {
+          const int o = (kc - 1) % NST;
+          if (!mbar_wait(&empty_bar[o], empty_phase[o])) { abort_flag = 1; break; }
+          empty_phase[o] ^= 1;
+          load_stage(o, kc - 1 + NST);
           tma_pending[o] = true;
         }
       }
@@ -271,20 +279,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (__syncthreads_or(!got || abort_flag)) { ok = false; break; }
     drain_phase ^= 1;
     tc_fence_after();
-    // drain: TMEM lanes 32 * quarter .. (tile rows), columns 32 * half .. of every level
-    const uint32_t lane_base = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    // drain: TMEM lanes 32 * quarter .. (tile rows), columns kCPT * half .. of every level
+    const uint32_t lane_base = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * kCPT);
 #pragma unroll
     for (int l = 0; l < kLevels; ++l) {
-      uint32_t r[32];
-      tmem_ld32(lane_base + (uint32_t)(l * kBN), r);
-      if (l < kHiLevels) {
-        const int sh = BITS * (kHiLevels - 1 - l);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) hi[c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
-      } else {
-        const int sh = BITS * (kLevels - 1 - l);
+      for (int c0 = 0; c0 < kCPT; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(lane_base + (uint32_t)(l * BN + c0), r);
+        if (l < kHiLevels) {
+          const int sh = BITS * (kHiLevels - 1 - l);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) lo[c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
+          for (int c = 0; c < 32; ++c) hi[c0 + c] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
+        } else {
+          const int sh = BITS * (kLevels - 1 - l);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) lo[(c0 + c) % kLoN] += (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
+        }
       }
     }
     tc_fence_before();
@@ -297,11 +308,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double whi = ldexp(1.0, -BITS * (kHiLevels + 1)), wlo = ldexp(1.0, -BITS * (S + 1));
       const int ei = ea[i];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int64_t j = (int64_t)bn * kBN + half * 32 + c;
+      for (int c = 0; c < kCPT; ++c) {
+        const int64_t j = (int64_t)bn * BN + half * kCPT + c;
         if (j >= N) continue;
         double* cp = C + i * sci + j * scj;
-        const double sum = fma((double)hi[c], whi, (kLoLevels > 0) ? (double)lo[c] * wlo : 0.0);
+        const double sum = fma((double)hi[c], whi, (kLoLevels > 0) ? (double)lo[c % kLoN] * wlo : 0.0);
         const double v = ldexp(alpha * sum, ei + fb[j]);
         *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
       }
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // give the copies and MMAs still in flight a bounded wait before TMEM is freed
     if (tid == 0) {
-      for (int st = 0; st < 2; ++st)
+      for (int st = 0; st < NST; ++st)
         if (tma_pending[st]) mbar_wait(&full_bar[st], tma_phase[st]);
       umma_commit(&drain_bar);
       mbar_wait(&drain_bar, drain_phase);
@@ -488,18 +499,18 @@ __global__ void mirror_upper_oz_kernel(double* C, int64_t n) {
   }
 }
 
-template <int S, int BITS, int KD>
+template <int S, int BITS, int KD, int BN, int NST>
 bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,
                const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
                cudaStream_t s, bool sym) {
-  const int64_t Mp = ceil_div(M, kBM) * kBM, Np = ceil_div(N, kBN) * kBN, Kp = ceil_div(K, kBK) * kBK;
-  if ((S * Mp) >= INT32_MAX || (S * Np) >= INT32_MAX || Np / kBN > 65535 || Kp >= INT32_MAX) return false;
+  const int64_t Mp = ceil_div(M, kBM) * kBM, Np = ceil_div(N, BN) * BN, Kp = ceil_div(K, kBK) * kBK;
+  if ((S * Mp) >= INT32_MAX || (S * Np) >= INT32_MAX || Np / BN > 65535 || Kp >= INT32_MAX) return false;
   // the int64 level accumulators take 2^{37 - 3 BITS} windows
   if (ceil_div(Kp, KD) > (1ll << (37 - 3 * BITS))) return false;
-  const size_t smem = 2 * (size_t)S * (kBM + kBN) * kBKs * 2 + 1024;
+  const size_t smem = (size_t)NST * S * (kBM + BN) * kBKs * 2 + 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(ozaki_gemm_kernel<S, BITS, KD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(ozaki_gemm_kernel<S, BITS, KD, BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
@@ -516,7 +527,7 @@ bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
 
   KClock clk;
   kclock_begin(clk, KC_GEMM_OZ, s);
-  ozaki_gemm_kernel<S, BITS, KD><<<dim3((unsigned)(Mp / kBM), (unsigned)(Np / kBN)), kThreads, smem, s>>>(
+  ozaki_gemm_kernel<S, BITS, KD, BN, NST><<<dim3((unsigned)(Mp / kBM), (unsigned)(Np / BN)), kThreads, smem, s>>>(
       qa.get(), same ? qa.get() : qb.get(), M, N, Kp, Mp, same ? Mp : Np, ea.get(), same ? ea.get() : fb.get(), alpha,
       beta, C, sci, scj, sym);
   FTT_LAUNCH();
@@ -550,8 +561,12 @@ bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const
   if (K <= 0) return false;
   // FP64 level: 8 slices of 7 bits (level sums exact over windows of 384: 384 x 40960 < 2^24);
   // FP32 level: 3 slices of 8 bits (windows of 192: 192 x 81920 < 2^24)
-  if (slices == 7) return run_ozaki<8, 7, 384>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
-  if (slices == 3) return run_ozaki<3, 8, 192>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  // FP64 level: 64-column tiles (8 levels x 64 TMEM columns), two-stage ring; FP32 level:
+  // 128-column tiles (3 levels x 128 columns), four-stage ring
+  if (slices == 7)
+    return run_ozaki<8, 7, 384, 64, 2>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
+  if (slices == 3)
+    return run_ozaki<3, 8, 192, 128, 4>(M, N, K, alpha, A, sai, sak, B, sbk, sbj, beta, C, sci, scj, s, sym);
   return false;
 }
 
