@@ -263,6 +263,7 @@ __device__ __forceinline__ double start_component(int64_t i, int64_t j) {
 // out [i * nv + t] so that a warp's accesses are contiguous.  The factors stay in
 // the scratch arrays (further solves: tri_solve).
 #define S(a, i) a[(int64_t)(i) * nv + t]
+
 template <typename T>
 __device__ void tri_solve(int64_t n, int64_t nv, int64_t t, const T* sdd, const T* sdu, const T* sdu2, const T* sdl,
                           const unsigned char* spiv, T* z, int64_t ldz) {
@@ -308,6 +309,7 @@ template <typename T>
 __global__ void inverse_iteration_kernel(const T* d, const T* e, int64_t n, const T* shift, int64_t j0, int64_t nv,
                                          T pert, T* sdd, T* sdu, T* sdu2, T* sdl, unsigned char* spiv, T* Z,
                                          int64_t ldz) {
+  constexpr int kInvIters = 3;   // fewer leave the refinement's start too rough (more Rayleigh-Ritz work)
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nv) return;
   const int64_t j = j0 + t;
@@ -347,17 +349,17 @@ __global__ void inverse_iteration_kernel(const T* d, const T* e, int64_t n, cons
   }
   T* z = Z + j;
   for (int64_t i = 0; i < n; ++i) z[i * ldz] = (T)start_component(i, j);
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < kInvIters; ++it) {
     tri_solve<T>(n, nv, t, sdd, sdu, sdu2, sdl, spiv, z, ldz);
     normalise_col<T>(n, z, ldz);
   }
 }
 
-// Clusters of close eigenvalues (block q: columns c0[2q] .. c0[2q+1]-1 of Z; the factors of every column in the scratch arrays, nv = n): subspace
-// iteration on the cluster, i.e. modified Gram-Schmidt of the cluster's columns
-// (twice), one more solve per column, and a final Gram-Schmidt.  Inverse
-// iteration alone returns nearly parallel vectors for eigenvalues closer than
-// its working accuracy; the cluster's span is still its invariant subspace.
+// Clusters of close eigenvalues (block q: columns c0[2q] .. c0[2q+1]-1 of Z):
+// modified Gram-Schmidt of the cluster's columns, twice.  Inverse iteration
+// returns nearly parallel vectors for eigenvalues closer than its working
+// accuracy, but from independent random starts they still span the cluster's
+// invariant subspace; the refinement that follows resolves the rest.
 template <typename T>
 __global__ void __launch_bounds__(256) cluster_orth_kernel(const int32_t* c0, int64_t n, int64_t nv, const T* sdd,
                                                            const T* sdu, const T* sdu2, const T* sdl,
@@ -399,14 +401,6 @@ __global__ void __launch_bounds__(256) cluster_orth_kernel(const int32_t* c0, in
         __syncthreads();
       }
   };
-  for (int it = 0; it < 2; ++it) {
-    gram_schmidt();
-    for (int64_t t = a + threadIdx.x; t < b; t += blockDim.x) {
-      tri_solve<T>(n, nv, t, sdd, sdu, sdu2, sdl, spiv, Z + t, ldz);
-      normalise_col<T>(n, Z + t, ldz);
-    }
-    __syncthreads();
-  }
   gram_schmidt();
 }
 #undef S
