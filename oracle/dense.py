@@ -122,6 +122,46 @@ def sequential_projection(A, eps, p, max_rank=0):
     return B, ranks
 
 
+def tt_round(cores, eps, max_rank=0):
+    """Alg. 2 (TT-rounding of a TT given by its cores), Section 2.4.
+
+    1. Right-to-left orthogonalisation: for k = d..2 the QR factorisation of the
+       transposed 1-unfolding of core k, unfold_1(G_k)^T = Q R; core k becomes Q^T
+       (its rows orthonormal) and R^T is absorbed into core k-1 (mode-3 product).
+    2. Afterwards ||A||_F = ||G_1||_F, and delta = eps ||A||_F / sqrt(d-1).
+    3. Left-to-right compression: for k = 1..d-1 the delta-truncated SVD of the
+       2-unfolding of core k, U S V^T; core k becomes U and S V^T is absorbed into
+       core k+1 (mode-1 product).
+    The rank rule is truncation_rank's, with eps = 0 meaning the numerical rank of
+    the k-unfolding of A (the tolerance numpy.linalg.matrix_rank uses for it).
+    Returns (cores, ranks, err2) with err2 the sum of the discarded sigma^2."""
+    G = [np.array(c, dtype=np.float64, copy=True) for c in cores]
+    d = len(G)
+    dims = [c.shape[1] for c in G]
+    for k in range(d - 1, 0, -1):
+        r0, n, r1 = G[k].shape
+        Q, R = np.linalg.qr(G[k].reshape(r0, n * r1).T, mode="reduced")   # (n r1) x q, q x r0
+        q = Q.shape[1]
+        G[k] = Q.T.reshape(q, n, r1)
+        a0, an, _ = G[k - 1].shape
+        G[k - 1] = (G[k - 1].reshape(a0 * an, r0) @ R.T).reshape(a0, an, q)
+    normA = math.sqrt(math.fsum((G[0] * G[0]).ravel()))
+    delta = eps * normA / math.sqrt(d - 1) if d > 1 else 0.0
+    ranks, err2 = [1], 0.0
+    for k in range(d - 1):
+        r0, n, r1 = G[k].shape
+        U, s, Vt = scipy.linalg.svd(G[k].reshape(r0 * n, r1), full_matrices=False, lapack_driver="gesvd")
+        tol = unfolding_rank_tol(dims, k + 1, s[0] if s.size else 0.0)
+        r = truncation_rank(s, delta, tol, max_rank)
+        err2 += float(np.sum(s[r:] ** 2))
+        G[k] = U[:, :r].reshape(r0, n, r)
+        b0, bn, b1 = G[k + 1].shape
+        G[k + 1] = ((s[:r, None] * Vt[:r]) @ G[k + 1].reshape(b0, bn * b1)).reshape(r, bn, b1)
+        ranks.append(r)
+    ranks.append(1)
+    return G, ranks, err2
+
+
 def tt_sum(a_cores, b_cores, beta=1.0):
     """Cores of A + beta*B by the block construction of Lemma 2 (eq. (6))."""
     d = len(a_cores)
