@@ -220,7 +220,7 @@ def run_ours(args):
     classes = {"gemm_f64_kernel": (st["ms_gemm"], st["flop_gemm"], "alu", FP64_PEAK_TFLOPS),
                "jacobi_sweep_kernel<double>": (st["ms_jacobi"], st["flop_jacobi"], "alu", FP64_PEAK_TFLOPS),
                "tridiag_kernel": (st["ms_tridiag"], st["flop_tridiag"], "alu", FP64_PEAK_TFLOPS),
-               "ozaki_gemm_kernel<8,7,384>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor", bf16_peak),
+               "ozaki_gemm_kernel<8,7,384,64,2>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor", bf16_peak),
                "tridiag_kernel<float>": (st["ms_tridiag32"], st["flop_tridiag32"], "alu", FP32_PEAK_TFLOPS),
                "qr_blocks_kernel+qr_apply_kernel": (st["ms_tsqr"], st["flop_tsqr"], "alu", FP64_PEAK_TFLOPS)}
     name, (kms, kwork, bound, peak) = max(classes.items(), key=lambda kv: kv[1][0])
