@@ -203,6 +203,7 @@ def run_ours(args):
     rel_err = _sampled_rel_err(F, idx, w, "fp64")
     mixed_line = None if args.no_mixed else _mixed(args, F, idx, vals, w, flush, stream)
     adjoint_line = None if args.no_adjoint else _adjoint(args, F, dev, stream)
+    round_line = None if args.no_tt_round else _tt_round(F, dev, stream)
 
     # e2e through the same C-ABI call from pinned host memory
     e2e_line = None
@@ -252,6 +253,7 @@ def run_ours(args):
             "rel_err_sampled": rel_err,
             "mixed": mixed_line,
             "adjoint": adjoint_line,
+            "tt_round": round_line,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm_oz", "ms_gemm",
@@ -350,6 +352,46 @@ def _adjoint(args, F, dev, stream):
     return out
 
 
+def _tt_round(F, dev, stream, reps=3):
+    """TT-rounding (Alg. 2) of the Lemma 2 sum S = A + B of two random 8-way 100^8 FP64
+    TTs of rank 64 (geometrically decaying bond spectra), ranks 128 in, eps = 1e-6.
+    Self-check through the library alone: the rounded R must satisfy
+    ||R - S||^2 = err2 (the truncations are orthogonal), with ||R - S|| taken from
+    the numerical-rank rounding of the Lemma 2 difference R - S."""
+    import math
+    import torch
+    from paper_1908_02721_gb300 import workloads as W
+    dims, ranks = [100] * 8, [1] + [64] * 7 + [1]
+    a = [torch.from_numpy(c).to(dev) for c in W.random_tt(dims, ranks, seed=501, decay=0.75)]
+    b = [torch.from_numpy(c).to(dev) for c in W.random_tt(dims, ranks, seed=502, decay=0.75)]
+    S = F.tt_add(a, b)
+    eps = 1e-6
+    F.tt_round(S, eps).free()
+    times = []
+    R = None
+    for _ in range(reps):
+        if R is not None:
+            R.free()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R = F.tt_round(S, eps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st = R.stats
+    Dlt = F.tt_add(R, S, beta=-1.0)
+    dn2 = F.tt_round(Dlt, 0.0).stats["norm2"]
+    out = {"workload": "A + B, two random 8-way 100^8 FP64 TTs of rank 64 (Lemma 2 sum, ranks 128), eps 1e-6",
+           "ms": sorted(times)[len(times) // 2], "ranks_in": S.ranks, "ranks_out": R.ranks,
+           "err2_rel": st["err2"] / st["norm2"], "measured_err_rel": math.sqrt(max(dn2, 0.0) / st["norm2"]),
+           "stages_ms": {k: st[k] for k in ("ms_gemm_oz", "ms_gemm", "ms_jacobi", "ms_tsqr", "ms_tridiag32",
+                                             "ms_tdeig")},
+           "launches": st["launches"]}
+    for h in (R, S, Dlt):
+        h.free()
+    return out
+
+
 def _e2e(args, w, F, dev, barrier, world):
     """Same call from pinned host buffers: H2D of the COO input and D2H of every core timed."""
     import torch
@@ -392,6 +434,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision pass")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-tt-round", action="store_true", help="skip the TT-rounding (Alg. 2) measurement")
     ap.add_argument("--workload", default="uniform5", choices=["uniform5", "uniform5-n30"],
                     help="uniform5-n30: the same recipe at 30^5, for profiler captures only")
     args = ap.parse_args()

@@ -180,6 +180,44 @@ int fasttt_tt_ranks(const fasttt_tt* tt, int64_t* ranks);
  * valid until fasttt_tt_free. */
 int fasttt_tt_core(const fasttt_tt* tt, int k, const double** d_core);
 
+/*
+ * fasttt_tt_round — Alg. 2 (TT-rounding of a TT given by its cores, Section 2.4):
+ * right-to-left orthogonalisation (core k's 1-unfolding factored by an
+ * untruncated SVD standing in for the QR factorisation, the orthonormal factor
+ * staying in core k and the rest multiplied into core k-1), then
+ * ||A||_F = ||G_1||_F, delta = eps ||A||_F / sqrt(d-1) and left-to-right
+ * delta-truncated SVDs of the 2-unfoldings, S V^T multiplied into the next core.
+ *
+ *  d, dims, ranks  order (1..FASTTT_MAX_D), host arrays of the d mode sizes and the
+ *                  d+1 ranks (r_0 = r_d = 1);
+ *  d_cores         host array of d device pointers, core k r_{k-1} x n_k x r_k FP64
+ *                  row-major (borrowed, only read; a handle's cores may be passed);
+ *  eps             relative accuracy (>= 0; 0 keeps the numerical ranks of the
+ *                  unfoldings, as fasttt_decompose);
+ *  opts            NULL for the defaults; read: precision, max_rank, max_sweeps,
+ *                  gemm_engine, keep_intermediates (singular values per bond);
+ *                  rounding must be FASTTT_STATIC;
+ *  out, stats      as fasttt_decompose (stats: ranks, norm2 = ||A||^2, err2 = the
+ *                  discarded sigma^2 summed over the bonds, deltas, stage times).
+ * Errors: EINVAL (bad sizes or ranks, null pointers, dynamic rounding), ENOMEM,
+ * ERANK, ETIMEOUT, ENUMERIC, ECUDA.
+ */
+int fasttt_tt_round(int d, const int64_t* dims, const int64_t* ranks, const double* const* d_cores,
+                    double eps, const fasttt_opts* opts, void* stream, fasttt_tt** out,
+                    fasttt_stats* stats);
+
+/*
+ * fasttt_tt_add — the TT of A + beta B (Lemma 2, eq. (6)) from the cores of two TTs
+ * with the same mode sizes: core 1 = [A_1, beta B_1], core d = [A_d; B_d], the cores
+ * in between block diagonal (d = 1: A_1 + beta B_1); ranks r_k^A + r_k^B.  Arguments
+ * as fasttt_tt_round (cores borrowed and only read); out receives a new handle whose
+ * stats hold d and the ranks only.  Round the sum with fasttt_tt_round.
+ * Errors: EINVAL, ENOMEM, ERANK, ECUDA.
+ */
+int fasttt_tt_add(int d, const int64_t* dims, const int64_t* ranks_a, const double* const* d_cores_a,
+                  const int64_t* ranks_b, const double* const* d_cores_b, double beta, void* stream,
+                  fasttt_tt** out);
+
 /* Arrays a handle can hand out with fasttt_tt_count / fasttt_tt_copy.  k is the
  * core index (1..d) or the bond index where noted; ignored otherwise. */
 #define FASTTT_ARR_CORE 0        /* f64, core k (r_{k-1} n_k r_k) */

@@ -66,10 +66,10 @@ inline void gemm(bool mixed, int64_t M, int64_t N, int64_t K, double alpha, cons
 int64_t jacobi_svd_f64(double* A, int64_t m, int64_t lda, int n, double* V, int64_t nv, int64_t ldv,
                        int64_t max_sweeps, cudaStream_t s);
 
-// The same result for a tall A (lg >> n, n <= kMaxTsqrCols) through Householder
-// TSQR (tsqr.cu): Jacobi on the n x n R only, then A <- Q (R V).  A is lg x n
-// column-major with leading dimension lg.
-constexpr int kMaxTsqrCols = 64;
+// The same result for a tall A (lg >= 1024, n <= kMaxTsqrCols) through Householder
+// TSQR (tsqr.cu): Jacobi on the stacked R factors only (at most 4n x n), then
+// A <- Q (R V).  A is lg x n column-major with leading dimension lg.
+constexpr int kMaxTsqrCols = 128;
 bool tsqr_applies(int64_t lg, int n);
 int64_t tsqr_jacobi(double* A, int64_t lg, int n, double* V, int64_t max_sweeps, cudaStream_t s);
 

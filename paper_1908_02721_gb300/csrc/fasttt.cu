@@ -190,6 +190,20 @@ __global__ void scale_rows_kernel(const double* Vt, int64_t r, int64_t N, const 
   GRID_STRIDE(e, r * N) out[e] = Vt[e] * sigma[e / N];
 }
 
+// Block construction of the TT sum (Lemma 2, eq. (6)): src (r0 x n x r1, row-major)
+// times scale goes to rows [o0, o0 + r0) and columns [o1, o1 + r1) of every slice
+// of dst (R0 x n x R1, row-major, zeroed by the caller); add = true accumulates
+// (the d = 1 sum, where both blocks cover the whole core).
+__global__ void place_block_kernel(const double* src, int64_t r0, int64_t n, int64_t r1, double scale, double* dst,
+                                   int64_t R1, int64_t o0, int64_t o1, bool add) {
+  GRID_STRIDE(e, r0 * n * r1) {
+    const int64_t c = e % r1, j = (e / r1) % n, i = e / (r1 * n);
+    double* t = dst + ((o0 + i) * n + j) * R1 + (o1 + c);
+    const double v = __dmul_rn(scale, src[e]);   // no FMA contraction: A + beta B rounded twice, as written
+    *t = add ? __dadd_rn(*t, v) : v;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- handle
@@ -604,6 +618,167 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   finish_block_stats(st, snap0);
 }
 
+// Checks a TT given by device cores: 1 <= d <= FASTTT_MAX_D, n_k >= 1, r_0 = r_d = 1,
+// r_k >= 1, no null core; returns the ranks and mode sizes as vectors.
+void check_tt(int d, const int64_t* dims, const int64_t* ranks, const double* const* cores, const char* what) {
+  const std::string w(what);
+  if (d < 1 || d > FASTTT_MAX_D) fail(FASTTT_EINVAL, w + ": d must be in 1..FASTTT_MAX_D");
+  if (!dims || !ranks || !cores) fail(FASTTT_EINVAL, w + ": null argument");
+  if (ranks[0] != 1 || ranks[d] != 1) fail(FASTTT_EINVAL, w + ": r_0 and r_d must be 1");
+  for (int k = 1; k <= d; ++k) {
+    if (dims[k - 1] < 1 || ranks[k] < 1) fail(FASTTT_EINVAL, w + ": mode sizes and ranks must be >= 1");
+    if (!cores[k - 1]) fail(FASTTT_EINVAL, w + ": null core");
+    if ((double)ranks[k - 1] * (double)dims[k - 1] * (double)ranks[k] > 0x1p40)
+      fail(FASTTT_ERANK, w + ": core too large");
+  }
+}
+
+// Alg. 2 (TT-rounding of a TT given by its cores), Section 2.4:
+//  1. right-to-left orthogonalisation, k = d..2: unfold_1(G_k) = (U S) V^T, untruncated
+//     (min(M,N) singular triplets, the size of the QR factorisation it stands for);
+//     G_k := V^T (orthonormal rows) and G_{k-1} := G_{k-1} x_3 (U S).  Nothing is
+//     dropped: in a Lemma 2 difference of close TTs the difference lives in the cores'
+//     small singular directions.  A direction whose singular value is exactly zero gets
+//     a zero row in V^T and a zero column in U S, which leaves the tensor and the
+//     singular values of the next sweep unchanged.
+//  2. ||A||_F = ||G_1||_F (the sum of the first bond's sigma^2), delta = eps ||A|| / sqrt(d-1).
+//  3. left-to-right compression, k = 1..d-1: delta-truncated SVD of unfold_2(G_k);
+//     G_k := U, G_{k+1} := (S V^T) x_1 G_{k+1}.
+// The rank rule, the eps = 0 reading and the max_rank cap are those of the
+// decomposition (S11).
+void round_tt(int d, const int64_t* dims, const int64_t* ranks, const double* const* cores, double eps,
+              const fasttt_opts& o, cudaStream_t s, Handle& H) {
+  check_tt(d, dims, ranks, cores, "tt_round");
+  if (!(eps >= 0.0) || !std::isfinite(eps)) fail(FASTTT_EINVAL, "eps must be finite and >= 0");
+  if (o.rounding != FASTTT_STATIC) fail(FASTTT_EINVAL, "tt_round: Alg. 2 fixes delta (static rounding only)");
+  if (o.precision != FASTTT_PREC_FP64 && o.precision != FASTTT_PREC_MIXED) fail(FASTTT_EINVAL, "unsupported precision");
+  if (o.gemm_engine != FASTTT_GEMM_TENSOR && o.gemm_engine != FASTTT_GEMM_DFMA) fail(FASTTT_EINVAL, "bad gemm_engine");
+  if (o.max_rank < 0) fail(FASTTT_EINVAL, "max_rank must be >= 0");
+  set_gemm_engine(o.gemm_engine);
+  const bool mixed = (o.precision == FASTTT_PREC_MIXED);
+  const bool eps0 = (eps == 0.0);
+  const int64_t max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
+  fasttt_stats& st = H.st;
+  st.d = d;
+  kclock_reset();
+  const int64_t launches0 = launch_count();
+  const CounterSnap snap0 = counter_snap();
+  Timer total(s);
+  std::vector<int64_t> n(dims, dims + d), r(ranks, ranks + d + 1);
+  std::vector<DBuf<double>> G(d + 1);   // 1-based
+  for (int k = 1; k <= d; ++k) {
+    G[k] = DBuf<double>((size_t)(r[k - 1] * n[k - 1] * r[k]), s);
+    FTT_CUDA(cudaMemcpyAsync(G[k].get(), cores[k - 1], G[k].bytes(), cudaMemcpyDeviceToDevice, s));
+  }
+  // 1. right-to-left orthogonalisation
+  for (int k = d; k >= 2; --k) {
+    const int64_t M = r[k - 1], N = n[k - 1] * r[k];
+    SvdOut sv;
+    svd_truncated(G[k].get(), M, N, [](const std::vector<double>& sg) { return (int64_t)sg.size(); }, max_sweeps,
+                  sv, s, mixed, 2);
+    st.jacobi_sweeps += sv.sweeps;
+    const int64_t q = sv.r;
+    G[k] = std::move(sv.Vt);
+    DBuf<double> US((size_t)(M * q), s);
+    scale_cols_kernel<<<grid_for(M * q), 256, 0, s>>>(sv.U.get(), M, q, sv.sigma.get(), US.get());
+    FTT_LAUNCH();
+    const int64_t Mp = r[k - 2] * n[k - 2];
+    DBuf<double> Gp((size_t)(Mp * q), s);
+    gemm(mixed, Mp, q, M, 1.0, G[k - 1].get(), M, 1, US.get(), q, 1, 0.0, Gp.get(), q, 1, s);
+    G[k - 1] = std::move(Gp);
+    r[k - 1] = q;
+  }
+  // 2.-3. norm from the first bond's singular values, then left-to-right compression
+  double normA = 0.0, delta = 0.0, err2 = 0.0;
+  if (d == 1) {
+    SvdOut sv;   // ||A|| of a one-mode TT: the single singular value of the 1 x n_1 core
+    svd_truncated(G[1].get(), 1, n[0], [](const std::vector<double>&) { return (int64_t)1; }, max_sweeps, sv, s,
+                  mixed, 0);
+    normA = sv.sigma_all.empty() ? 0.0 : sv.sigma_all[0];
+  }
+  for (int k = 1; k <= d - 1; ++k) {
+    const int64_t M = r[k - 1] * n[k - 1], N = r[k];
+    SvdOut sv;
+    svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) {
+      if (k == 1) {
+        double acc = 0.0;
+        for (size_t i = sg.size(); i-- > 0;) acc += sg[i] * sg[i];
+        normA = std::sqrt(acc);
+        delta = eps * normA / std::sqrt((double)(d - 1));
+      }
+      return rank_rule(sg, delta, eps0, n, k, o.max_rank);
+    }, max_sweeps, sv, s, mixed, 1);
+    st.jacobi_sweeps += sv.sweeps;
+    err2 += tail2(sv.sigma_all, sv.r);
+    st.deltas[k] = delta;
+    if (o.keep_intermediates) {
+      if (H.sigmas.empty()) H.sigmas.assign(d + 1, {});
+      H.sigmas[k] = sv.sigma_all;
+    }
+    const int64_t rr = sv.r;
+    G[k] = std::move(sv.U);
+    DBuf<double> W((size_t)(rr * N), s);
+    scale_rows_kernel<<<grid_for(rr * N), 256, 0, s>>>(sv.Vt.get(), rr, N, sv.sigma.get(), W.get());
+    FTT_LAUNCH();
+    const int64_t N1 = n[k] * r[k + 1];
+    DBuf<double> Gn((size_t)(rr * N1), s);
+    gemm(mixed, rr, N1, N, 1.0, W.get(), N, 1, G[k + 1].get(), N1, 1, 0.0, Gn.get(), N1, 1, s);
+    G[k + 1] = std::move(Gn);
+    r[k] = rr;
+  }
+  st.norm2 = normA * normA;
+  st.err2 = err2;
+  H.d = d;
+  H.dims = n;
+  H.ranks = r;
+  H.cores.clear();
+  for (int k = 1; k <= d; ++k) H.cores.push_back(std::move(G[k]));
+  for (int k = 0; k <= d; ++k) st.ranks[k] = r[k];
+  H.kept = o.keep_intermediates != 0;
+  st.ms_round = total.lap();
+  st.ms_total = st.ms_round;
+  ozaki_take_timeout(s);
+  finish_stats(st, launches0);
+  finish_block_stats(st, snap0);
+}
+
+// Lemma 2 (eq. (6)): the cores of A + beta B.  Core 1 is [A_1, beta B_1] (columns),
+// core d is [A_d; B_d] (rows), the cores in between are block diagonal; for d = 1
+// the single core is A_1 + beta B_1.  Ranks r_k^A + r_k^B for 0 < k < d.
+void add_tt(int d, const int64_t* dims, const int64_t* ranks_a, const double* const* cores_a, const int64_t* ranks_b,
+            const double* const* cores_b, double beta, cudaStream_t s, Handle& H) {
+  check_tt(d, dims, ranks_a, cores_a, "tt_add (A)");
+  check_tt(d, dims, ranks_b, cores_b, "tt_add (B)");
+  if (!std::isfinite(beta)) fail(FASTTT_EINVAL, "tt_add: beta must be finite");
+  const int64_t launches0 = launch_count();
+  Timer total(s);
+  std::vector<int64_t> n(dims, dims + d), r(d + 1, 1);
+  for (int k = 1; k < d; ++k) r[k] = ranks_a[k] + ranks_b[k];
+  H.cores.clear();
+  for (int k = 1; k <= d; ++k) {
+    const int64_t ra0 = ranks_a[k - 1], ra1 = ranks_a[k], rb0 = ranks_b[k - 1], rb1 = ranks_b[k], nk = n[k - 1];
+    DBuf<double> C((size_t)(r[k - 1] * nk * r[k]), s);
+    FTT_CUDA(cudaMemsetAsync(C.get(), 0, C.bytes(), s));
+    const bool one = (d == 1);
+    const int64_t ob0 = (k == 1) ? 0 : ra0, ob1 = (k == d) ? 0 : ra1;   // offsets of B's block
+    place_block_kernel<<<grid_for(ra0 * nk * ra1), 256, 0, s>>>(cores_a[k - 1], ra0, nk, ra1, 1.0, C.get(), r[k], 0, 0,
+                                                                false);
+    FTT_LAUNCH();
+    place_block_kernel<<<grid_for(rb0 * nk * rb1), 256, 0, s>>>(cores_b[k - 1], rb0, nk, rb1, k == 1 ? beta : 1.0,
+                                                                C.get(), r[k], one ? 0 : ob0, one ? 0 : ob1, one);
+    FTT_LAUNCH();
+    H.cores.push_back(std::move(C));
+  }
+  fasttt_stats& st = H.st;
+  st.d = d;
+  H.d = d;
+  H.dims = n;
+  H.ranks = r;
+  for (int k = 0; k <= d; ++k) st.ranks[k] = r[k];
+  st.ms_total = total.lap();
+  st.launches = launch_count() - launches0;
+}
+
 int handle_error(const Error& e) {
   g_last_error = e.what();
   return e.code;
@@ -616,6 +791,42 @@ void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 }  // namespace fasttt
 
 using namespace fasttt;
+
+namespace {
+// Runs body (which fills a fresh handle) under the ABI's error conventions.
+template <class F>
+int make_handle(void* stream, fasttt_tt** out, fasttt_stats* stats, F&& body) {
+  g_last_error.clear();
+  if (!out) {
+    g_last_error = "null argument";
+    return FASTTT_EINVAL;
+  }
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::unique_ptr<fasttt_tt> tt(new fasttt_tt());
+  int rc = FASTTT_OK;
+  try {
+    body(s, tt->h);
+  } catch (const Error& e) {
+    rc = handle_error(e);
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    rc = FASTTT_ECUDA;
+  }
+  if (stats) *stats = tt->h.st;
+  if (rc != FASTTT_OK) {
+    cudaStreamSynchronize(s);
+    return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("CUDA error: ") + cudaGetErrorString(e);
+    return FASTTT_ECUDA;
+  }
+  *out = tt.release();
+  return FASTTT_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -667,6 +878,24 @@ int fasttt_decompose(int d, const int64_t* dims, int64_t nnz, const int32_t* d_i
   }
   *out = tt.release();
   return FASTTT_OK;
+}
+
+int fasttt_tt_round(int d, const int64_t* dims, const int64_t* ranks, const double* const* d_cores, double eps,
+                    const fasttt_opts* opts, void* stream, fasttt_tt** out, fasttt_stats* stats) {
+  fasttt_opts o;
+  if (opts) o = *opts;
+  else fasttt_default_opts(&o);
+  return make_handle(stream, out, stats, [&](cudaStream_t s, Handle& H) {
+    round_tt(d, dims, ranks, d_cores, eps, o, s, H);
+  });
+}
+
+int fasttt_tt_add(int d, const int64_t* dims, const int64_t* ranks_a, const double* const* d_cores_a,
+                  const int64_t* ranks_b, const double* const* d_cores_b, double beta, void* stream,
+                  fasttt_tt** out) {
+  return make_handle(stream, out, nullptr, [&](cudaStream_t s, Handle& H) {
+    add_tt(d, dims, ranks_a, d_cores_a, ranks_b, d_cores_b, beta, s, H);
+  });
 }
 
 void fasttt_tt_free(fasttt_tt* tt) {

@@ -110,6 +110,12 @@ _lib.tt_eval_backward.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P)
                                   _P, _P, ctypes.POINTER(_P), ctypes.c_int, _P]
 _lib.tt_eval_backward_noalloc.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int,
                                           ctypes.c_int64, _P, _P, ctypes.POINTER(_P), _P]
+_lib.fasttt_tt_round.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_double,
+                                 ctypes.POINTER(Opts), _P, ctypes.POINTER(_P), ctypes.POINTER(Stats)]
+_lib.fasttt_tt_round.restype = ctypes.c_int
+_lib.fasttt_tt_add.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
+                               ctypes.c_double, _P, ctypes.POINTER(_P)]
+_lib.fasttt_tt_add.restype = ctypes.c_int
 _lib.fasttt_last_error.restype = ctypes.c_char_p
 _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
@@ -123,7 +129,7 @@ EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
            "tt_eval_backward_noalloc",
            "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig",
-           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd"]
+           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd", "fasttt_tt_round", "fasttt_tt_add"]
 
 
 class FastTTError(RuntimeError):
@@ -322,6 +328,69 @@ def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True
     rc = _lib.fasttt_decompose(d, _i64arr(dims), int(idx.shape[1]), ctypes.c_void_p(idx.data_ptr()),
                                ctypes.c_void_p(vals.data_ptr()), vdtype, float(eps), ctypes.byref(o),
                                _stream(stream), ctypes.byref(out), ctypes.byref(st))
+    _check(rc)
+    return TT(out.value, dims)
+
+
+def _fp64_tt(x):
+    """(d, dims, ranks, core pointer array, keep-alive) of a TT handle (borrowed cores)
+    or of a list of FP64 CUDA cores (r_{k-1}, n_k, r_k)."""
+    if isinstance(x, TT):
+        ptrs = (ctypes.c_void_p * x.d)()
+        for k in range(1, x.d + 1):
+            p = ctypes.c_void_p(0)
+            _check(_lib.fasttt_tt_core(x._h, k, ctypes.byref(p)))
+            ptrs[k - 1] = p.value
+        return x.d, list(x.dims), list(x.ranks), ptrs, x
+    cores = [_dev(G, torch.float64) for G in x]
+    if not cores or any(G.dim() != 3 for G in cores):
+        raise FastTTError(EINVAL, "cores must be a non-empty list of (r0, n, r1) tensors")
+    d = len(cores)
+    dims = [int(G.shape[1]) for G in cores]
+    ranks = [int(cores[0].shape[0])] + [int(G.shape[2]) for G in cores]
+    if any(int(cores[k].shape[0]) != ranks[k] for k in range(d)):
+        raise FastTTError(EINVAL, "core ranks do not chain")
+    ptrs = (ctypes.c_void_p * d)(*[G.data_ptr() for G in cores])
+    return d, dims, ranks, ptrs, cores
+
+
+def tt_round(tt, eps, *, max_rank=0, precision="fp64", max_sweeps=0, gemm_engine="tensor",
+             keep_intermediates=False, stream=None) -> TT:
+    """TT-rounding (Alg. 2) of a TT given as a handle or as FP64 CUDA cores, to relative
+    accuracy eps (eps = 0: numerical ranks); max_rank caps every rank.  Returns a new handle."""
+    _require_cuda()
+    d, dims, ranks, ptrs, keep = _fp64_tt(tt)
+    o = Opts()
+    _lib.fasttt_default_opts(ctypes.byref(o))
+    o.max_rank = int(max_rank)
+    o.max_sweeps = int(max_sweeps)
+    o.keep_intermediates = 1 if keep_intermediates else 0
+    if precision not in ("fp64", "mixed"):
+        raise FastTTError(EINVAL, "precision must be 'fp64' or 'mixed'")
+    o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+    if gemm_engine not in GEMM_ENGINES:
+        raise FastTTError(EINVAL, "gemm_engine must be 'tensor' or 'dfma'")
+    o.gemm_engine = GEMM_ENGINES[gemm_engine]
+    out = ctypes.c_void_p(0)
+    st = Stats()
+    rc = _lib.fasttt_tt_round(d, _i64arr(dims), _i64arr(ranks), ptrs, float(eps), ctypes.byref(o), _stream(stream),
+                              ctypes.byref(out), ctypes.byref(st))
+    del keep
+    _check(rc)
+    return TT(out.value, dims)
+
+
+def tt_add(a, b, beta=1.0, stream=None) -> TT:
+    """Cores of A + beta B (Lemma 2) for TTs given as handles or FP64 CUDA cores."""
+    _require_cuda()
+    d, dims, ra, pa, keep_a = _fp64_tt(a)
+    db, dims_b, rb, pb, keep_b = _fp64_tt(b)
+    if db != d or dims_b != dims:
+        raise FastTTError(EINVAL, "tt_add: the TTs have different mode sizes")
+    out = ctypes.c_void_p(0)
+    rc = _lib.fasttt_tt_add(d, _i64arr(dims), _i64arr(ra), pa, _i64arr(rb), pb, float(beta), _stream(stream),
+                            ctypes.byref(out))
+    del keep_a, keep_b
     _check(rc)
     return TT(out.value, dims)
 

@@ -254,3 +254,17 @@ CONFIGS = {
     1: exact_small,
     2: uniform5,
 }
+
+
+def random_tt(dims, ranks, seed: int, decay: float = 1.0):
+    """Cores of a random TT (r_{k-1}, n_k, r_k), N(0,1) entries, FP64.  decay < 1
+    scales slice j of every core's right bond by decay**j, so the unfoldings'
+    singular values fall off geometrically (well-separated truncation points)."""
+    rng = _rng(seed)
+    cores = []
+    for k, n in enumerate(dims):
+        G = rng.standard_normal((ranks[k], n, ranks[k + 1]))
+        if decay != 1.0:
+            G = G * (decay ** np.arange(ranks[k + 1]))[None, None, :]
+        cores.append(G)
+    return cores

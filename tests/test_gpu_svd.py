@@ -59,7 +59,9 @@ def _check(F, Z, full_rank=True):
     assert np.linalg.norm(Vt[:k] @ Vt[:k].T - np.eye(k)) <= 4 * tol
 
 
-TSQR_SHAPES = [(125000, 50), (50, 125000), (1024, 2), (5000, 64), (70000, 33), (2048 + 7, 17)]
+TSQR_SHAPES = [(125000, 50), (50, 125000), (1024, 2), (5000, 64), (70000, 33), (2048 + 7, 17),
+               # 64 < n <= 128: blocks of 224 rows, tree stopped at <= 4n stacked rows
+               (12800, 128), (128, 12800), (1024, 65), (30000 + 13, 100)]
 
 
 @pytest.mark.parametrize("shape", TSQR_SHAPES)
@@ -67,13 +69,13 @@ def test_tall_skinny_gaussian(F, shape):
     _check(F, _matrix(*shape, "gaussian", seed=shape[0] + shape[1]))
 
 
-@pytest.mark.parametrize("shape", [(20000, 40), (40, 20000), (3000, 64)])
+@pytest.mark.parametrize("shape", [(20000, 40), (40, 20000), (3000, 64), (12800, 128)])
 def test_tall_skinny_graded(F, shape):
     """Singular values over 14 decades: the small ones are resolved to u sigma_1."""
     _check(F, _matrix(*shape, "graded", seed=7 + shape[0]))
 
 
-@pytest.mark.parametrize("shape", [(20000, 40), (3000, 60)])
+@pytest.mark.parametrize("shape", [(20000, 40), (3000, 60), (5000, 120)])
 def test_tall_skinny_rank_deficient(F, shape):
     _check(F, _matrix(*shape, "rank_deficient", seed=9 + shape[0]), full_rank=False)
 
