@@ -119,6 +119,18 @@ def _oracle_step(w):
     return time.perf_counter() - t
 
 
+def _max_over_ranks(x, device):
+    """Max of a per-rank number over all ranks (the slowest replica sets the job's time);
+    the number itself when no process group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -192,11 +204,7 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - t0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(sum(step_ms) / args.steps, dev)
     value = w.nnz * world / (ms / 1e3)
 
     # accuracy of the timed configuration: relative error of B at a fixed sample of nonzeros
