@@ -58,3 +58,29 @@ def tt_eval_grad(cores, idx, g):
         np.add.at(dG, (slice(None), idx[k], slice(None)), np.transpose(contrib, (1, 0, 2)))
         grads.append(dG)
     return grads
+
+
+def tt_fit_loss(cores, idx, vals):
+    """L = 1/2 sum_e (a(i^e) - v_e)^2 over the given entries (math.fsum of the squares)."""
+    import math
+    r = tt_eval_at_batched(cores, idx) - np.asarray(vals, dtype=np.float64)
+    return 0.5 * math.fsum((r * r).tolist())
+
+
+def tt_fit_gd(cores, idx, vals, steps, lr):
+    """Fixed-rank fitting of a TT to entries (the completion use of fixed-rank TTs,
+    Section 3.4) by plain gradient descent with the adjoint of the entry formula:
+    every step evaluates the residual r_e = a(i^e) - v_e, takes the gradient of
+    L = 1/2 sum r_e^2, which is the adjoint with upstream weights g_e = r_e, and moves
+    all cores at once, G_k <- G_k - lr dL/dG_k.  Returns the new cores (FP64) and the
+    steps + 1 losses (before every step and after the last)."""
+    cores = [np.array(G, dtype=np.float64, copy=True) for G in cores]
+    v = np.asarray(vals, dtype=np.float64)
+    losses = []
+    for _ in range(steps):
+        r = tt_eval_at_batched(cores, idx) - v
+        losses.append(tt_fit_loss(cores, idx, v))
+        grads = tt_eval_grad(cores, idx, r)
+        cores = [G - lr * dG for G, dG in zip(cores, grads)]
+    losses.append(tt_fit_loss(cores, idx, v))
+    return cores, losses
