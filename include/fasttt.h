@@ -301,6 +301,29 @@ int tt_eval_backward_noalloc(int d, const int64_t* dims, const int64_t* ranks,
                              const void* const* d_cores, int dtype, int64_t m, const int32_t* d_idx,
                              const void* d_grad_out, void* const* d_grad_cores, void* stream);
 
+/*
+ * tt_fit_gd — fixed-rank fitting of a TT to given entries (the tensor-completion
+ * use of fixed-rank TT approximations, Sec. 3.4) by plain gradient descent with
+ * the adjoint of the entry formula (Sec. 2.3).  Each step evaluates the residual
+ * r_e = a(i^e) - v_e, takes the gradient of L = 1/2 sum_e r_e^2 (the adjoint with
+ * upstream weights r_e) and moves every core from the same point:
+ * G_k <- G_k - lr dL/dG_k (product and difference rounded separately).
+ *  d, dims, ranks, dtype  as tt_eval_at; the ranks stay fixed;
+ *  d_cores                host array of d device pointers, UPDATED IN PLACE;
+ *  m, d_idx, d_vals       the m entries: (d, m) int32 indices (0-based, SoA) and
+ *                         their values in the cores' dtype;
+ *  steps, lr              number of steps (>= 0) and the step length;
+ *  h_losses               host array of steps + 1 doubles: L before every step
+ *                         and after the last (FP64 sums of the squared residuals).
+ * Scratch (residuals, one gradient per core, the adjoint's partials) is allocated
+ * on the device for the call.  Synchronous with respect to the host.
+ * Errors: EINVAL (bad sizes, null pointers, negative steps, non-finite lr, an index
+ * out of range), ERANK, ENOMEM, ECUDA.
+ */
+int tt_fit_gd(int d, const int64_t* dims, const int64_t* ranks, void* const* d_cores, int dtype,
+              int64_t m, const int32_t* d_idx, const void* d_vals, int64_t steps, double lr,
+              double* h_losses, void* stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char* fasttt_last_error(void);
 

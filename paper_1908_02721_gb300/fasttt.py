@@ -116,6 +116,9 @@ _lib.fasttt_tt_round.restype = ctypes.c_int
 _lib.fasttt_tt_add.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
                                ctypes.c_double, _P, ctypes.POINTER(_P)]
 _lib.fasttt_tt_add.restype = ctypes.c_int
+_lib.tt_fit_gd.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64, _P, _P,
+                           ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P]
+_lib.tt_fit_gd.restype = ctypes.c_int
 _lib.fasttt_last_error.restype = ctypes.c_char_p
 _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
@@ -129,7 +132,7 @@ EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
            "tt_eval_backward_noalloc",
            "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig",
-           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd", "fasttt_tt_round", "fasttt_tt_add"]
+           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd", "fasttt_tt_round", "fasttt_tt_add", "tt_fit_gd"]
 
 
 class FastTTError(RuntimeError):
@@ -407,6 +410,24 @@ def _core_args(cores):
     ranks = [int(cores[0].shape[0])] + [int(G.shape[2]) for G in cores]
     ptrs = (ctypes.c_void_p * d)(*[G.data_ptr() for G in cores])
     return d, dims, ranks, ptrs, (F64 if dtype == torch.float64 else F32), dtype
+
+
+def tt_fit_gd(cores, idx, vals, steps, lr, stream=None):
+    """Fixed-rank fitting of the TT to the entries (idx (d, m) int32, vals (m,) in the
+    cores' dtype) by gradient descent with the adjoint; the cores (contiguous CUDA
+    tensors) are updated in place.  Returns the steps + 1 losses 1/2 sum (a - v)^2."""
+    _require_cuda()
+    d, dims, ranks, ptrs, code, dtype = _core_args(cores)
+    idx = _dev(idx, torch.int32)
+    vals = _dev(vals, dtype)
+    if idx.dim() != 2 or idx.shape[0] != d or vals.shape != (idx.shape[1],):
+        raise FastTTError(EINVAL, "idx must be (d, m) and vals (m,)")
+    losses = np.zeros(int(steps) + 1, dtype=np.float64)
+    rc = _lib.tt_fit_gd(d, _i64arr(dims), _i64arr(ranks), ptrs, code, int(idx.shape[1]),
+                        ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(vals.data_ptr()), int(steps), float(lr),
+                        losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream))
+    _check(rc)
+    return losses
 
 
 def tt_eval_at(cores, idx, stream=None) -> torch.Tensor:
