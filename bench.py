@@ -357,7 +357,32 @@ def _adjoint(args, F, dev, stream):
         out[f"rank{r}"] = {"eval_ms": fwd, "backward_ms": bwd, "backward_gbs": bytes_bwd / (bwd / 1e3) / 1e9,
                            "backward_hbm_frac": bytes_bwd / (bwd / 1e3) / 1e9 / hbm,
                            "backward_tflops": flops_bwd / (bwd / 1e3) / 1e12}
+        if r == 8:
+            out["fit_rank8"] = _fit(F, cores, idx, w, dev, stream, m)
     return out
+
+
+def _fit(F, cores, idx, w, dev, stream, m, steps=3, lr=1e-9):
+    """Gradient-descent fitting (tt_fit_gd) of the rank-8 FP32 TT to the workload's 1e7
+    values: time per step (evaluation, residual, adjoint, descent).  A small step keeps
+    the measurement away from divergence; a failure is reported in the object."""
+    import math
+    import torch
+    try:
+        vals = torch.from_numpy(w.vals).to(dev)
+        fc = [c.clone() for c in cores]
+        F.tt_fit_gd(fc, idx, vals, 1, lr)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        losses = F.tt_fit_gd(fc, idx, vals, steps, lr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        fin = [float(x) if math.isfinite(x) else None for x in (losses[0], losses[-1])]
+        return {"steps": steps, "lr": lr, "ms_per_step": ms, "entries_per_s": m / (ms / 1e3),
+                "loss_first": fin[0], "loss_last": fin[1]}
+    except Exception as e:   # reported, never hidden
+        return {"error": str(e)[:300]}
 
 
 def _tt_round(F, dev, stream, reps=3):
