@@ -82,3 +82,29 @@ def test_calls_without_gpu_fail_loudly(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(F.FastTTError):
         F.fasttt_decompose([[0, 1], [1, 0]], [1.0, 2.0], [2, 2], 0.0)
+
+
+def test_tt_arithmetic_and_fitting_fail_loudly_without_gpu(lib):
+    """The entry points added for TT arithmetic and fitting have no CPU path either:
+    the binding refuses before the call and the library itself rejects bad
+    arguments or reports the missing device."""
+    import torch
+    from paper_1908_02721_gb300 import fasttt as F
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cores = [torch.zeros((1, 2, 1), dtype=torch.float64)]
+    for call in (lambda: F.tt_round(cores, 0.1), lambda: F.tt_add(cores, cores),
+                 lambda: F.tt_fit_gd(cores, [[0]], [1.0], 1, 0.1)):
+        with pytest.raises(F.FastTTError) as e:
+            call()
+        assert e.value.code == F.ECUDA
+    # straight through the C ABI: argument checks run first, then no device
+    out = ctypes.c_void_p(0)
+    dims = (ctypes.c_int64 * 1)(2)
+    bad_ranks = (ctypes.c_int64 * 2)(2, 1)
+    ptrs = (ctypes.c_void_p * 1)(None)
+    assert lib.fasttt_tt_round(1, dims, bad_ranks, ptrs, ctypes.c_double(0.1), None, None,
+                               ctypes.byref(out), None) == F.EINVAL
+    losses = (ctypes.c_double * 2)()
+    assert lib.tt_fit_gd(0, dims, bad_ranks, ptrs, 0, ctypes.c_int64(0), None, None, ctypes.c_int64(1),
+                         ctypes.c_double(0.1), losses, None) == F.EINVAL
