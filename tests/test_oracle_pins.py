@@ -331,3 +331,42 @@ def test_tt_sum_and_diff_norm():
     assert np.allclose(D.tt_full(D.tt_sum(a, b)), D.tt_full(a) + D.tt_full(b), atol=1e-13)
     ref = np.linalg.norm(D.tt_full(a) - D.tt_full(b))
     assert abs(D.tt_diff_norm(a, b) - ref) <= 1e-13 * ref
+
+
+def test_value_depar_hand_worked_example():
+    """S6 on the hand-worked example of tests/golden/depar_example.txt (Alg. 3 with exact
+    parallelism on the rows of X, then on the columns of D): classes, prefactors, D',
+    Lambda_S, Lambda_T and C exactly as derived by hand."""
+    rec = {}
+    X, DP, C = [], [], []
+    path = os.path.join(os.path.dirname(__file__), "golden", "depar_example.txt")
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        tag, *rest = line.split()
+        if tag == "X":
+            X.append((int(rest[0]), int(rest[1]), float(rest[2])))
+        elif tag == "DP":
+            DP.append((int(rest[0]), int(rest[1]), float(rest[2])))
+        elif tag == "C":
+            C.append((int(rest[0]), int(rest[1]), float(rest[2])))
+        else:
+            rec[tag] = [float(x) for x in rest]
+    rows = np.array([x[0] for x in X])
+    cols = np.array([x[1] for x in X])
+    vals = np.array([x[2] for x in X])
+    dp = F.value_depar(rows, cols, vals)
+    assert dp.row_ids.tolist() == [int(x) for x in rec["ROWS"]]
+    assert dp.row_class.tolist() == [int(x) for x in rec["ROW_CLASS"]]
+    assert dp.row_pref.tolist() == rec["ROW_PREF"]
+    assert dp.col_ids.tolist() == [int(x) for x in rec["COLS"]]
+    assert dp.col_class.tolist() == [int(x) for x in rec["COL_CLASS"]]
+    assert dp.col_pref.tolist() == rec["COL_PREF"]
+    got_dp = sorted(zip(dp.dp_rows.tolist(), dp.dp_cols.tolist(), dp.dp_vals.tolist()))
+    assert got_dp == sorted(DP)
+    assert dp.lam_s.tolist() == rec["LAM_S"] and dp.lam_t.tolist() == rec["LAM_T"]
+    Cd = F.depar_dense_C(dp)
+    want = np.zeros((3, 3))
+    for i, j, v in C:
+        want[i, j] = v
+    assert np.array_equal(Cd, want)
