@@ -370,3 +370,36 @@ def test_value_depar_hand_worked_example():
     for i, j, v in C:
         want[i, j] = v
     assert np.array_equal(Cd, want)
+
+
+def test_grouping_hand_worked_example():
+    """S2-S5 on the hand-worked example of tests/golden/grouping_example.txt: the
+    lexicographic-rank ids of both sweeps, the P-cores' (parent, index) and
+    (index, child) maps, r~, R (eq. (4)) and the middle unfolding."""
+    rec, nz, mid = {}, [], []
+    path = os.path.join(os.path.dirname(__file__), "golden", "grouping_example.txt")
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        tag, *rest = line.split()
+        if tag == "NZ":
+            nz.append(([int(x) for x in rest[:4]], float(rest[4])))
+        elif tag == "MID":
+            mid.append((int(rest[0]), int(rest[1]), float(rest[2])))
+        else:
+            rec[tag] = [int(x) for x in rest]
+    dims, p = rec["DIMS"], rec["P"][0]
+    idx = np.array([i for i, _ in nz]).T
+    v = np.array([x for _, x in nz])
+    tt = F.exact_tt(idx, v, dims, p)
+    assert tt.R == rec["R"][0]
+    assert list(tt.rt) == rec["RT"]
+    l1, l2 = rec["LEFT1"], rec["LEFT2"]
+    assert tt.left[0][0].tolist() == l1[:2] and tt.left[0][1].tolist() == l1[2:]
+    assert tt.left[1][0].tolist() == l2[:4] and tt.left[1][1].tolist() == l2[4:]
+    r4 = rec["RIGHT4"]
+    assert tt.right[0][0].tolist() == r4[:3] and tt.right[0][1].tolist() == r4[3:]
+    assert tt.alpha_left.tolist() == rec["ALPHA_L"] and tt.alpha_right.tolist() == rec["ALPHA_R"]
+    got = sorted(zip(tt.mid_rows.tolist(), tt.mid_cols.tolist(), tt.mid_vals.tolist()))
+    assert got == sorted(mid)
+    assert tuple(tt.mid_shape) == (rec["RT"][2] * dims[2], rec["RT"][3])
