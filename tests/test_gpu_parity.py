@@ -80,6 +80,63 @@ def test_alg9_split_selection(F, case):
     assert tt.stats["p"] == p
 
 
+def _golden(name):
+    import os
+    rec, rows = {}, {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        if not line.strip() or line.startswith("#"):
+            continue
+        tag, *rest = line.split()
+        rows.setdefault(tag, []).append(rest)
+    return rows
+
+
+def test_grouping_hand_worked_example_on_gpu(F):
+    """The hand-derived ids, P-core maps, r~, R and middle unfolding of
+    tests/golden/grouping_example.txt, bit for bit."""
+    g = _golden("grouping_example.txt")
+    dims = [int(x) for x in g["DIMS"][0]]
+    p = int(g["P"][0][0])
+    idx = np.ascontiguousarray(np.array([[int(x) for x in r[:4]] for r in g["NZ"]], dtype=np.int32).T)
+    vals = np.array([float(r[4]) for r in g["NZ"]])
+    tt = F.fasttt_decompose(idx, vals, dims, 0.0, p=p, stage="exact", keep_intermediates=True)
+    ints = lambda tag: [int(x) for x in g[tag][0]]
+    assert tt.stats["R"] == ints("R")[0] and tt.stats["rt"] == ints("RT")
+    l1, l2, r4 = ints("LEFT1"), ints("LEFT2"), ints("RIGHT4")
+    assert _np(tt.array("left_parent", 1)).tolist() == l1[:2] and _np(tt.array("left_index", 1)).tolist() == l1[2:]
+    assert _np(tt.array("left_parent", 2)).tolist() == l2[:4] and _np(tt.array("left_index", 2)).tolist() == l2[4:]
+    assert _np(tt.array("right_index", 4)).tolist() == r4[:3] and _np(tt.array("right_child", 4)).tolist() == r4[3:]
+    mid = sorted((int(r[0]), int(r[1]), float(r[2])) for r in g["MID"])
+    got = list(zip(_np(tt.array("mid_row")).tolist(), _np(tt.array("mid_col")).tolist(),
+                   _np(tt.array("mid_val")).tolist()))
+    assert got == mid
+    tt.free()
+
+
+def test_value_depar_hand_worked_example_on_gpu(F):
+    """The 6 x 5 matrix of tests/golden/depar_example.txt as a 2-way tensor at p = 1 (its
+    middle unfolding is the matrix itself): classes, prefactors, D' and Lambda as
+    derived by hand, bit for bit."""
+    g = _golden("depar_example.txt")
+    idx = np.ascontiguousarray(np.array([[int(r[0]), int(r[1])] for r in g["X"]], dtype=np.int32).T)
+    vals = np.array([float(r[2]) for r in g["X"]])
+    tt = F.fasttt_decompose(idx, vals, [6, 5], 0.1, p=1, keep_intermediates=True)
+    ints = lambda tag: [int(x) for x in g[tag][0]]
+    flts = lambda tag: [float(x) for x in g[tag][0]]
+    assert _np(tt.array("row_id")).tolist() == ints("ROWS")
+    assert _np(tt.array("row_class")).tolist() == ints("ROW_CLASS")
+    assert _np(tt.array("row_pref")).tolist() == flts("ROW_PREF")
+    assert _np(tt.array("col_id")).tolist() == ints("COLS")
+    assert _np(tt.array("col_class")).tolist() == ints("COL_CLASS")
+    assert _np(tt.array("col_pref")).tolist() == flts("COL_PREF")
+    dp = sorted(zip(_np(tt.array("dp_row")).tolist(), _np(tt.array("dp_col")).tolist(),
+                    _np(tt.array("dp_val")).tolist()))
+    assert dp == sorted((int(r[0]), int(r[1]), float(r[2])) for r in g["DP"])
+    assert _np(tt.array("lam_s")).tolist() == flts("LAM_S")
+    assert _np(tt.array("lam_t")).tolist() == flts("LAM_T")
+    tt.free()
+
+
 # ---------------------------------------------------------------- S6: bit-exact value Depar
 
 def _depar_check(F, w, p):
