@@ -217,6 +217,8 @@ def run_ours(args):
     e2e_line = None
     if not args.no_e2e:
         e2e_line = _e2e(args, w, F, dev, barrier, world)
+    # last: extension timings, each guarded (nothing after them depends on the device)
+    next_line = None if args.no_tt_round else _next_rows(F, dev, stream)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
@@ -262,6 +264,7 @@ def run_ours(args):
             "mixed": mixed_line,
             "adjoint": adjoint_line,
             "tt_round": round_line,
+            "next_rows": next_line,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm_oz", "ms_gemm",
@@ -383,6 +386,51 @@ def _fit(F, cores, idx, w, dev, stream, m, steps=3, lr=1e-9):
                 "loss_first": fin[0], "loss_last": fin[1]}
     except Exception as e:   # reported, never hidden
         return {"error": str(e)[:300]}
+
+
+def _next_rows(F, dev, stream):
+    """One timed decomposition for each extension that runs through fasttt_decompose:
+    dynamic truncation (Alg. 8) on the 50^5 workload, and the FDM 7-point matrices of
+    Table 2 (3-way MPO, p = 2, eps = 1e-14) at n = 20, 30, 40.  Each after one warm-up
+    call; failures are reported in the object."""
+    import torch
+    from paper_1908_02721_gb300 import workloads as W
+
+    def timed(call):
+        call().free()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tt = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return tt, e0.elapsed_time(e1)
+
+    out = {}
+    try:
+        w = W.uniform5(seed=2)
+        idx, vals = torch.from_numpy(w.idx).to(dev), torch.from_numpy(w.vals).to(dev)
+        tt, ms = timed(lambda: F.fasttt_decompose(idx, vals, w.dims, w.eps, rounding="dynamic"))
+        st = tt.stats
+        out["dynamic_alg8"] = {"workload": "5-way 50^5, 1e5 nnz, eps 1e-8, FP64", "ms": ms,
+                               "nnz_per_s": w.nnz / (ms / 1e3), "ranks": tt.ranks,
+                               "err_bound_used": (st["err2"] / st["norm2"]) ** 0.5}
+        tt.free()
+    except Exception as e:
+        out["dynamic_alg8"] = {"error": str(e)[:300]}
+    fdm = {}
+    for n in (20, 30, 40):
+        for coeffs in ("pattern", "random"):
+            key = f"n{n}_{coeffs}"
+            try:
+                w = W.fdm7(n, coeffs)
+                idx, vals = torch.from_numpy(w.idx).to(dev), torch.from_numpy(w.vals).to(dev)
+                tt, ms = timed(lambda: F.fasttt_decompose(idx, vals, w.dims, w.eps, p=2))
+                fdm[key] = {"nnz": w.nnz, "ms": ms, "R": tt.stats["R"], "rt": tt.stats["rt"], "ranks": tt.ranks}
+                tt.free()
+            except Exception as e:
+                fdm[key] = {"error": str(e)[:300]}
+    out["fdm7_table2"] = fdm
+    return out
 
 
 def _tt_round(F, dev, stream, reps=3):
