@@ -330,6 +330,23 @@ const char* fasttt_last_error(void);
 /* Library version string. */
 const char* fasttt_version(void);
 
+/* Host-only test hooks (no device work; callable without a GPU).
+ * fasttt_debug_select_p: the split index p of Alg. 9 that fasttt_decompose takes for
+ * mode sizes dims (d of them) and the nonzero p-fiber counts Rs[p-1] (eq. (4)): the
+ * argmin over p of eq. (13) with the bounds of eq. (10) (r capped at max_rank when
+ * > 0), exact in 128-bit integers (saturating at 2^128 - 1), ties to the smallest p.
+ * Returns p in 1..d, or EINVAL (d outside 2..FASTTT_MAX_D, a size or R outside
+ * 1..2^31-1, max_rank < 0).
+ * fasttt_debug_rank_rule: the rank r_k the rounding takes at bond `bond` (1..d-1)
+ * from the n singular values h_sigma (descending, host): eps_zero = 0: the smallest
+ * r >= 1 whose tail sqrt(sum_{i>r} sigma_i^2) (summed from the smallest up) is <= delta;
+ * eps_zero = 1: the count of sigma_i > max(M,N) 2^-52 sigma_1 with M x N the size of
+ * the bond's unfolding of the d-way tensor (at least 1); then min(r, max_rank) when
+ * max_rank > 0.  Returns r, or EINVAL. */
+int fasttt_debug_select_p(int d, const int64_t* dims, const int64_t* Rs, int64_t max_rank);
+int64_t fasttt_debug_rank_rule(const double* h_sigma, int64_t n, double delta, int eps_zero, int d,
+                               const int64_t* dims, int bond, int64_t max_rank);
+
 /* Test hook for the host-side failure paths: the n-th device allocation from now
  * (n >= 1) fails with ENOMEM; n = 0 disables it.  Affects the calling process. */
 void fasttt_debug_fail_alloc_after(int64_t n);

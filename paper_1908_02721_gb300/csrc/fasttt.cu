@@ -1035,6 +1035,34 @@ void fasttt_debug_fail_alloc_after(int64_t n) {
   g_fail_after = n > 0 ? n : 0;
 }
 
+int fasttt_debug_select_p(int d, const int64_t* dims, const int64_t* Rs, int64_t max_rank) {
+  g_last_error.clear();
+  try {
+    if (d < 2 || d > FASTTT_MAX_D || !dims || !Rs || max_rank < 0) fail(FASTTT_EINVAL, "select_p: bad arguments");
+    for (int k = 0; k < d; ++k) {
+      if (dims[k] < 1 || dims[k] > INT32_MAX) fail(FASTTT_EINVAL, "select_p: mode sizes must be in 1..2^31-1");
+      if (Rs[k] < 1 || Rs[k] > INT32_MAX) fail(FASTTT_EINVAL, "select_p: R must be in 1..2^31-1");
+    }
+    return select_p_host(std::vector<int64_t>(dims, dims + d), std::vector<int64_t>(Rs, Rs + d), max_rank);
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
+}
+
+int64_t fasttt_debug_rank_rule(const double* h_sigma, int64_t n, double delta, int eps_zero, int d,
+                               const int64_t* dims, int bond, int64_t max_rank) {
+  g_last_error.clear();
+  try {
+    if (!h_sigma || n < 1 || d < 2 || d > FASTTT_MAX_D || !dims || bond < 1 || bond >= d || max_rank < 0 ||
+        !(delta >= 0.0))
+      fail(FASTTT_EINVAL, "rank_rule: bad arguments");
+    return rank_rule(std::vector<double>(h_sigma, h_sigma + n), delta, eps_zero != 0,
+                     std::vector<int64_t>(dims, dims + d), bond, max_rank);
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
+}
+
 int fasttt_debug_gemm(int64_t M, int64_t N, int64_t K, const double* d_A, const double* d_B, double* d_C, int engine,
                       void* stream) {
   try {

@@ -169,7 +169,9 @@ int64_t sat_prod(const std::vector<int64_t>& dims, int a, int b, int64_t cap) {
   return (int64_t)p;
 }
 
-u128 f_svd(u128 m, u128 n) { return m * n * (m < n ? m : n); }
+u128 f_svd(u128 m, u128 n) { return m * n * (m < n ? m : n); }   // < 2^124: m <= 2^62, n, min <= 2^31
+
+u128 sat_add(u128 a, u128 b) { return (a + b < a) ? ~(u128)0 : a + b; }   // a sum of d terms may pass 2^128
 
 }  // namespace
 
@@ -186,8 +188,8 @@ int select_p_host(const std::vector<int64_t>& dims, const std::vector<int64_t>& 
     }
     // eq. (13) with 1-based mode sizes n_i = dims[i-1]
     u128 f = f_svd((u128)rt[p - 1] * dims[p - 1], (u128)rt[p]);
-    for (int i = p + 1; i <= d - 1; ++i) f += f_svd((u128)r[i - 1] * dims[i - 1], (u128)rt[i]);
-    for (int i = 2; i <= p; ++i) f += f_svd((u128)rt[i - 1], (u128)dims[i - 1] * r[i]);
+    for (int i = p + 1; i <= d - 1; ++i) f = sat_add(f, f_svd((u128)r[i - 1] * dims[i - 1], (u128)rt[i]));
+    for (int i = 2; i <= p; ++i) f = sat_add(f, f_svd((u128)rt[i - 1], (u128)dims[i - 1] * r[i]));
     if (p == 1 || f < best_f) {
       best = p;
       best_f = f;

@@ -119,6 +119,11 @@ _lib.fasttt_tt_add.restype = ctypes.c_int
 _lib.tt_fit_gd.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64, _P, _P,
                            ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _P]
 _lib.tt_fit_gd.restype = ctypes.c_int
+_lib.fasttt_debug_select_p.argtypes = [ctypes.c_int, _I64P, _I64P, ctypes.c_int64]
+_lib.fasttt_debug_select_p.restype = ctypes.c_int
+_lib.fasttt_debug_rank_rule.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int, _I64P, ctypes.c_int, ctypes.c_int64]
+_lib.fasttt_debug_rank_rule.restype = ctypes.c_int64
 _lib.fasttt_last_error.restype = ctypes.c_char_p
 _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
@@ -132,7 +137,8 @@ EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
            "tt_eval_backward_noalloc",
            "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig",
-           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd", "fasttt_tt_round", "fasttt_tt_add", "tt_fit_gd"]
+           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd", "fasttt_tt_round", "fasttt_tt_add", "tt_fit_gd",
+           "fasttt_debug_select_p", "fasttt_debug_rank_rule"]
 
 
 class FastTTError(RuntimeError):
@@ -152,6 +158,24 @@ def version() -> str:
 
 def debug_fail_alloc_after(n: int) -> None:
     _lib.fasttt_debug_fail_alloc_after(int(n))
+
+
+def debug_select_p(dims, Rs, max_rank=0) -> int:
+    """Alg. 9's split index as the library's host code computes it (no device work)."""
+    p = _lib.fasttt_debug_select_p(len(dims), _i64arr(dims), _i64arr(Rs), int(max_rank))
+    if p < 0:
+        raise FastTTError(p, _lib.fasttt_last_error().decode())
+    return int(p)
+
+
+def debug_rank_rule(sigma, delta, eps_zero, dims, bond, max_rank=0) -> int:
+    """The rounding's rank decision at `bond` as the library's host code takes it (no device work)."""
+    s = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+    r = _lib.fasttt_debug_rank_rule(s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), s.size, float(delta),
+                                    1 if eps_zero else 0, len(dims), _i64arr(dims), int(bond), int(max_rank))
+    if r < 0:
+        raise FastTTError(int(r), _lib.fasttt_last_error().decode())
+    return int(r)
 
 
 EIG_METHODS = {"tridiagonal": 0, "iterative": 1, "auto": 2, "fast": 3}
