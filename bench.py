@@ -389,10 +389,12 @@ def _fit(F, cores, idx, w, dev, stream, m, steps=3, lr=1e-9):
 
 
 def _next_rows(F, dev, stream):
-    """One timed decomposition for each extension that runs through fasttt_decompose:
-    dynamic truncation (Alg. 8) on the 50^5 workload, and the FDM 7-point matrices of
-    Table 2 (3-way MPO, p = 2, eps = 1e-14) at n = 20, 30, 40.  Each after one warm-up
-    call; failures are reported in the object."""
+    """One timed decomposition for each extension and further workload that runs through
+    fasttt_decompose: dynamic truncation (Alg. 8) on the 50^5 workload; the FDM 7-point
+    matrices of Table 2 (3-way MPO, p = 2, eps = 1e-14) at n = 20, 30, 40; the banded
+    2^20 x 2^20 matrix as a 20-way QTT through the exact grouping (S1-S5), and the
+    2^12 x 2^12 one through the whole pipeline in FP64 and mixed precision.  Each after one
+    warm-up call; failures are reported in the object."""
     import torch
     from paper_1908_02721_gb300 import workloads as W
 
@@ -430,6 +432,28 @@ def _next_rows(F, dev, stream):
             except Exception as e:
                 fdm[key] = {"error": str(e)[:300]}
     out["fdm7_table2"] = fdm
+    qtt = {}
+    try:   # the sparse-matrix -> QTT workload at full size: S1-S5 (exact grouping, Alg. 9 over all 20 splits)
+        w = W.banded_qtt(20)
+        idx, vals = torch.from_numpy(w.idx).to(dev), torch.from_numpy(w.vals).to(dev)
+        tt, ms = timed(lambda: F.fasttt_decompose(idx, vals, w.dims, w.eps, stage="exact"))
+        st = tt.stats
+        qtt["m20_exact_grouping"] = {"workload": w.name, "nnz": w.nnz, "ms": ms, "nnz_per_s": w.nnz / (ms / 1e3),
+                                     "p": st["p"], "R": st["R"], "rt_max": max(st["rt"])}
+        tt.free()
+    except Exception as e:
+        qtt["m20_exact_grouping"] = {"error": str(e)[:300]}
+    for prec in ("fp64", "mixed"):   # the whole pipeline where its ranks stay dense-sized
+        try:
+            w = W.banded_qtt(12)
+            idx, vals = torch.from_numpy(w.idx).to(dev), torch.from_numpy(w.vals).to(dev)
+            tt, ms = timed(lambda: F.fasttt_decompose(idx, vals, w.dims, w.eps, precision=prec))
+            qtt[f"m12_{prec}"] = {"workload": w.name, "nnz": w.nnz, "ms": ms, "p": tt.stats["p"],
+                                  "rank_max": max(tt.ranks), "rel_err_sampled": _sampled_rel_err(F, idx, w, prec, tt)}
+            tt.free()
+        except Exception as e:
+            qtt[f"m12_{prec}"] = {"error": str(e)[:300]}
+    out["banded_qtt"] = qtt
     return out
 
 
