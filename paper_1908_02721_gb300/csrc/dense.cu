@@ -632,8 +632,9 @@ int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ld
       bj_smem = bytes(b, vrows);
       bj_vec = ((uintptr_t)A % 16 == 0) && ((uintptr_t)V % 16 == 0) && ((size_t)lda * sizeof(T)) % 16 == 0 &&
                ((size_t)ldv * sizeof(T)) % 16 == 0;
+      // the whole budget (not this call's need), so that concurrent callers never lower it for each other
       FTT_CUDA(cudaFuncSetAttribute(jacobi_block_sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)bj_smem));
+                                    (int)budget));
       int per = 0;
       FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_block_sweep_kernel<T>, 32 * bj_wpp * b,
                                                              bj_smem));

@@ -508,14 +508,11 @@ bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
   // the int64 level accumulators take 2^{37 - 3 BITS} windows
   if (ceil_div(Kp, KD) > (1ll << (37 - 3 * BITS))) return false;
   const size_t smem = (size_t)NST * S * (kBM + BN) * kBKs * 2 + 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(ozaki_gemm_kernel<S, BITS, KD, BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    attr_set = true;
+  // set on every call: the limit belongs to the current device's context
+  if (cudaFuncSetAttribute(ozaki_gemm_kernel<S, BITS, KD, BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
   const bool same = (A == B && M == N && sai == sbj && sak == sbk);
   DBuf<__nv_bfloat16> qa((size_t)S * Mp * Kp, s), qb(same ? 0 : (size_t)S * Np * Kp, s);

@@ -167,15 +167,13 @@ template <int BR>
 int64_t tsqr_jacobi_br(double* A, int64_t lg, int n, double* V, int64_t max_sweeps, cudaStream_t s) {
   const size_t smem_qr = sizeof(double) * (size_t)BR * n;
   const size_t smem_ap = sizeof(double) * (size_t)BR * (n + 1);
-  static bool attr = false;
-  if (!attr) {
-    const int ncap = (BR == kQrRowsNarrow) ? 64 : kMaxTsqrCols;
-    FTT_CUDA(cudaFuncSetAttribute(qr_blocks_kernel<BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(double) * (size_t)BR * ncap)));
-    FTT_CUDA(cudaFuncSetAttribute(qr_apply_kernel<BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(double) * (size_t)BR * (ncap + 1))));
-    attr = true;
-  }
+  // set on every call (the limit belongs to the current device's context), always to the
+  // instantiation's largest need, so that concurrent callers never lower it for each other
+  const int ncap = (BR == kQrRowsNarrow) ? 64 : kMaxTsqrCols;
+  FTT_CUDA(cudaFuncSetAttribute(qr_blocks_kernel<BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * (size_t)BR * ncap)));
+  FTT_CUDA(cudaFuncSetAttribute(qr_apply_kernel<BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * (size_t)BR * (ncap + 1))));
   // level l: input X_l (rows_l x n, leading dimension ld_l); level 0 is A itself.  The
   // tree stops once the stacked R factors have at most 4n rows (or one block remained).
   std::vector<double*> X{A};

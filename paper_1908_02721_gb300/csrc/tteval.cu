@@ -214,7 +214,8 @@ int warps_for(K kernel, int64_t rmax, int vecs, size_t esz, size_t* smem) {
   int64_t w = std::min<int64_t>(kMaxWarps, kSmemBudget / per_warp);
   if (w < 1) fail(FASTTT_ERANK, "TT rank too large for the shared-memory vectors");
   *smem = (size_t)(w * per_warp);
-  FTT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+  // always the budget (not this call's need), so that concurrent callers never lower it for each other
+  FTT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
   return (int)w;
 }
 
