@@ -566,7 +566,9 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   FTT_CUDA(cudaMemcpyAsync(A.get(), G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   // 1. tridiagonalisation
   {
-    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the route's whole budget (not this call's need), so that concurrent callers never lower it
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max - 4096));
     int per = 0;
     FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<double>, 256, smem));
     const int grid = std::min(2, per) * sms;
@@ -706,7 +708,9 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   FTT_LAUNCH();
   // 1. FP32 tridiagonalisation
   {
-    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the route's whole budget (not this call's need), so that concurrent callers never lower it
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max - 4096));
     int per = 0;
     FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<float>, 256, smem));
     const int grid = std::min(2, per) * sms;
