@@ -219,6 +219,10 @@ def run_ours(args):
         e2e_line = _e2e(args, w, F, dev, barrier, world)
     # last: extension timings, each guarded (nothing after them depends on the device)
     next_line = None if args.no_tt_round else _next_rows(F, dev, stream)
+    if adjoint_line is not None and "_fit_args" in adjoint_line:
+        cores8, aidx, aw, am = adjoint_line.pop("_fit_args")
+        adjoint_line["fit_rank8"] = _fit(F, cores8, aidx, aw, dev, stream, am)
+        del cores8, aidx, aw
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
@@ -362,8 +366,8 @@ def _adjoint(args, F, dev, stream):
         out[f"rank{r}"] = {"eval_ms": fwd, "backward_ms": bwd, "backward_gbs": bytes_bwd / (bwd / 1e3) / 1e9,
                            "backward_hbm_frac": bytes_bwd / (bwd / 1e3) / 1e9 / hbm,
                            "backward_tflops": flops_bwd / (bwd / 1e3) / 1e12}
-        if r == 8:
-            out["fit_rank8"] = _fit(F, cores, idx, w, dev, stream, m)
+        if r == 8:   # the fitting runs after every other measurement (see run_ours)
+            out["_fit_args"] = (cores, idx, w, m)
     return out
 
 
