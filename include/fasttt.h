@@ -77,6 +77,9 @@ typedef struct fasttt_opts {
   int64_t max_sweeps; /* Jacobi sweep bound of the dense SVDs; 0 = default (40) */
   int sparse_sweep;   /* first SVD sweep (Alg. 6) bonds: FASTTT_SWEEP_AUTO, _SPARSE or _DENSE */
   int gemm_engine;    /* FASTTT_GEMM_TENSOR (default) or FASTTT_GEMM_DFMA */
+  int64_t max_spin;   /* polls of every device-side spin-wait (grid barriers, tensor-core
+                         pipeline waits) before it gives up and the call fails with
+                         FASTTT_ETIMEOUT; 0 = default (2^24 barrier polls, 2^22 pipeline polls) */
 } fasttt_opts;
 
 /* Engine of the dense FP64 contractions.  TENSOR: products of at least 2^26
@@ -139,6 +142,10 @@ typedef struct fasttt_stats {
   double ms_tridiag32, flop_tridiag32; /* FP32 tridiagonalisation of the fast eigensolver's start (2 n^3 flops) */
   double ms_tsqr, flop_tsqr;  /* Householder TSQR of tall-skinny SVDs and its Q application (4 m n^2 flops each) */
   int64_t eig_fast;           /* Gram eigenproblems solved by the fast route (FP32 start + refinement) */
+  int64_t qr_cholqr2;         /* QR steps of Alg. 6's right-to-left sweep done by CholeskyQR2 */
+  int64_t qr_svd;             /* QR steps that fell back to an untruncated SVD (CholeskyQR2 broke down) */
+  int64_t mixed_fp32_bonds;   /* mixed precision: Gram-route SVDs whose FP32-level result was kept */
+  int64_t mixed_fp64_bonds;   /* mixed precision: Gram-route SVDs redone with FP64-level products */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */
@@ -372,6 +379,18 @@ int fasttt_debug_sym_eig(const double* d_G, int64_t n, double* d_V, double* h_la
  * tensor-core kernel declined or gave up.  Synchronises the stream. */
 int fasttt_debug_gemm(int64_t M, int64_t N, int64_t K, const double* d_A, const double* d_B, double* d_C, int engine,
                       void* stream);
+
+/* Test hook for CholeskyQR2 (the QR factorisation of Alg. 6's right-to-left
+ * sweep, and the re-orthonormalisation of the mixed precision; the paper names
+ * a QR factorisation only).  d_Z: M x N FP64 row-major device array, M <= N,
+ * overwritten by Q (orthonormal rows); d_R: M x M device array (caller-allocated)
+ * receives the upper triangular R with Z = R^T Q.  precision FASTTT_PREC_MIXED:
+ * the Grams and the solve updates are FP32-level products (the Cholesky
+ * factorisations stay FP64).  FASTTT_ENUMERIC when a Cholesky factorisation
+ * breaks down or the second Gram is further than 0.5 from I (Z too ill
+ * conditioned for the Gram's precision); FASTTT_EINVAL for bad arguments.
+ * Synchronises the stream. */
+int fasttt_debug_cholqr(int64_t M, int64_t N, double* d_Z, double* d_R, int precision, void* stream);
 
 /* Test hook for the dense SVD of the rounding sweeps (the paper has no
  * counterpart; it exposes the SVD behind S7-S10 so that it can be checked on

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <numeric>
 
@@ -1105,69 +1106,6 @@ bool refine_eig(const double* G, int n, double* V, std::vector<double>& lam_out,
   return true;
 }
 
-// Orthonormalise the columns of the row-major rows x r matrix U on the tensor
-// cores: U <- U + 0.5 U (I - U^T U), twice (quadratic while ||I - U^T U|| < 1).
-void orthonormalise_cols_tc(double* U, int64_t rows, int64_t r, cudaStream_t s) {
-  DBuf<double> S((size_t)r * r, s), U0((size_t)rows * r, s);
-  for (int it = 0; it < 2; ++it) {
-    gemm(true, r, r, rows, 1.0, U, 1, r, U, r, 1, 0.0, S.get(), r, 1, s, true);   // U^T U
-    i_minus_kernel<<<grid_for(r * r), 256, 0, s>>>(S.get(), r);
-    FTT_LAUNCH();
-    FTT_CUDA(cudaMemcpyAsync(U0.get(), U, sizeof(double) * rows * r, cudaMemcpyDeviceToDevice, s));
-    gemm(true, rows, r, r, 0.5, U0.get(), r, 1, S.get(), r, 1, 1.0, U, r, 1, s);
-  }
-}
-
-// out[i] = (row i of X) . (row i of Y), den[i] = |row i of X|^2 (n x n row-major, FP64 sums)
-__global__ void row_dots_kernel(const double* X, const double* Y, int64_t n, double* num, double* den) {
-  const int64_t i = blockIdx.x;
-  double a = 0.0, b = 0.0, z = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-    const double x = X[i * n + j];
-    a = fma(x, Y[i * n + j], a);
-    b = fma(x, x, b);
-  }
-  block_sum3<double>(a, b, z);
-  if (threadIdx.x == 0) { num[i] = a; den[i] = b; }
-}
-
-// Mixed-precision eigendecomposition of the symmetric PSD Gram G (n x n): FP32
-// one-sided Jacobi to FP32 convergence gives V; the eigenvalues are the Rayleigh
-// quotients v^T G v / v^T v with G V on the tensor cores and the dot products in
-// FP64.  FP32-level accuracy; the caller re-orthonormalises what it keeps.
-int64_t sym_eig_mixed32(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps,
-                        cudaStream_t s) {
-  const int64_t nn = (int64_t)n * n;
-  int64_t sweeps;
-  {
-    DBuf<float> G32(nn, s), V32(nn, s);
-    to_f32_kernel<<<grid_for(nn), 256, 0, s>>>(G, nn, G32.get());
-    FTT_LAUNCH();
-    identity_f32_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), n);
-    FTT_LAUNCH();
-    sweeps = jacobi<float>(G32.get(), n, n, n, V32.get(), n, n, max_sweeps, s);
-    if (sweeps < 0) fail(FASTTT_ETIMEOUT, "FP32 Jacobi did not converge within the sweep bound");
-    to_f64_kernel<<<grid_for(nn), 256, 0, s>>>(V32.get(), nn, V);
-    FTT_LAUNCH();
-  }
-  // FP32 rotations accumulated over all sweeps leave V orthonormal only to ~1e-4:
-  // restore it (columns of V = rows of its row-major memory)
-  DBuf<double> W(nn, s), num(n, s), den(n, s);
-  transpose_f64(V, n, n, W.get(), s);
-  orthonormalise_cols_tc(W.get(), n, n, s);
-  transpose_f64(W.get(), n, n, V, s);
-  gemm_tf32x3(n, n, n, 1.0, V, n, 1, G, n, 1, 0.0, W.get(), n, 1, s);   // row i = (G v_i)^T
-  row_dots_kernel<<<n, 256, 0, s>>>(V, W.get(), n, num.get(), den.get());
-  FTT_LAUNCH();
-  std::vector<double> hn(n), hd(n);
-  FTT_CUDA(cudaMemcpyAsync(hn.data(), num.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-  FTT_CUDA(cudaMemcpyAsync(hd.data(), den.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-  FTT_CUDA(cudaStreamSynchronize(s));
-  lam_out.resize(n);
-  for (int i = 0; i < n; ++i) lam_out[i] = hd[i] > 0.0 ? hn[i] / hd[i] : 0.0;
-  return sweeps;
-}
-
 }  // namespace
 
 int64_t jacobi_svd_f64(double* A, int64_t m, int64_t lda, int n, double* V, int64_t nv, int64_t ldv,
@@ -1213,56 +1151,128 @@ void transpose_f64(const double* src, int64_t rows, int64_t cols, double* dst, c
   FTT_LAUNCH();
 }
 
-void svd_truncated(const double* Z, int64_t M, int64_t N,
-                   const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
-                   SvdOut& out, cudaStream_t s, bool mixed, int ortho) {
-  const bool tall = (M >= N);
-  const int64_t sm = tall ? N : M;   // number of singular values
-  const int64_t lg = tall ? M : N;
-  if (sm > INT32_MAX / 2) fail(FASTTT_ERANK, "SVD too large");
-  const int n = (int)sm;
-  // direct (accurate) route while a Jacobi sweep stays below ~4e10 flops
-  const bool direct = (sm <= kDirectMax) || (9.0 * (double)lg * (double)sm * (double)sm <= 4.0e10);
-  DBuf<double> A;      // column-major lg x n (direct) or n x n (Gram)
-  int64_t m_len, lda;
-  if (direct) {
-    A = DBuf<double>((size_t)lg * n, s);
-    if (tall) transpose_f64(Z, M, N, A.get(), s);  // columns of Z become contiguous
-    else FTT_CUDA(cudaMemcpyAsync(A.get(), Z, sizeof(double) * M * N, cudaMemcpyDeviceToDevice, s));
-    m_len = lg;
-    lda = lg;
-  } else {
-    A = DBuf<double>((size_t)n * n, s);
-    if (tall)  // G = Z^T Z
-      gemm(mixed, N, N, M, 1.0, Z, 1, N, Z, N, 1, 0.0, A.get(), N, 1, s, true);
-    else       // G = Z Z^T
-      gemm(mixed, M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, A.get(), M, 1, s, true);
-    m_len = n;
-    lda = n;
+namespace {
+
+// Counters of the mixed-precision Gram route (bonds kept at FP32 level, bonds
+// redone with FP64-level products), read into the statistics.
+std::atomic<int64_t> g_mixed_kept{0}, g_mixed_escalated{0};
+
+// Kept eigenvalues must lie this many times above the Gram route's error floor
+// for an FP32-level result to be used.
+constexpr double kResolve = 64.0;
+
+// sigma = sqrt(max(lambda, 0)) sorted descending with the permutation that sorts them.
+void sigma_from_lambda(const std::vector<double>& h, std::vector<double>& sig, std::vector<int32_t>& perm) {
+  const int n = (int)h.size();
+  perm.resize(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::vector<double> sv(n);
+  for (int i = 0; i < n; ++i) {
+    sv[i] = sqrt(std::max(h[i], 0.0));
+    if (!std::isfinite(sv[i])) fail(FASTTT_ENUMERIC, "non-finite singular value");
   }
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return sv[a] > sv[b]; });
+  sig.resize(n);
+  for (int i = 0; i < n; ++i) sig[i] = sv[perm[i]];
+}
+
+// Whether an FP32-level spectrum can decide this bond: the rank chosen does not
+// change when every eigenvalue sigma_i^2 moves by +-floor, and the kept ones lie
+// kResolve * floor or more above zero.  choose_rank is called on the perturbed
+// spectra only; the caller calls it once more on the spectrum it keeps.
+bool rank_is_resolved(const std::function<int64_t(const std::vector<double>&)>& choose_rank,
+                      const std::vector<double>& sig, int64_t nkeep, double floor) {
+  const int64_t n = (int64_t)sig.size();
+  if (n == 0) return true;
+  const int64_t r0 = std::max<int64_t>(1, std::min<int64_t>(choose_rank(sig), nkeep));
+  const double sr = sig[r0 - 1];
+  if (!(sr * sr >= kResolve * floor)) return false;
+  std::vector<double> up(n), dn(n);
+  for (int64_t i = 0; i < n; ++i) {
+    up[i] = sqrt(sig[i] * sig[i] + floor);
+    dn[i] = sqrt(std::max(sig[i] * sig[i] - floor, 0.0));
+  }
+  const int64_t ru = std::max<int64_t>(1, std::min<int64_t>(choose_rank(up), nkeep));
+  const int64_t rd = std::max<int64_t>(1, std::min<int64_t>(choose_rank(dn), nkeep));
+  return ru == r0 && rd == r0;
+}
+
+// The FP32 start of the Gram eigensolver, kept so that a bond redone at FP64 level
+// refines the same start instead of computing it again.
+struct EigStart {
+  DBuf<double> V;
+  std::vector<double> lam;
+  bool ok = false;
+};
+
+// Eigenpairs of the symmetric Gram G (n x n) into V (row j = eigenvector j) and h.
+// mixed: FP32 start + FP32-level refinement, false when either declines.  FP64
+// level: the stored start refined with FP64-level products if there is one, else
+// the fast route, then the FP64 tridiagonal route, then the iterative one.
+bool gram_eig(const double* G, int n, double* V, std::vector<double>& h, int64_t max_sweeps, cudaStream_t s,
+              bool mixed, EigStart& st0, int64_t& sweeps) {
+  sweeps = 0;
+  const int64_t nn = (int64_t)n * n;
+  if (mixed) {
+    if (!sym_eig_start_f32(G, n, V, h, s)) return false;
+    st0.V = DBuf<double>(nn, s);
+    FTT_CUDA(cudaMemcpyAsync(st0.V.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    st0.lam = h;
+    st0.ok = true;
+    if (!refine_eig(G, n, V, h, max_sweeps, s, true)) return false;
+    note_eig_fast();
+    return true;
+  }
+  if (st0.ok) {
+    FTT_CUDA(cudaMemcpyAsync(V, st0.V.get(), sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    h = st0.lam;
+    if (refine_eig(G, n, V, h, max_sweeps, s, false)) {
+      note_eig_fast();
+      return true;
+    }
+  } else if (sym_eig_fast(G, n, V, h, max_sweeps, s, false)) {
+    return true;
+  }
+  const bool td = sym_eig_tridiag(G, n, V, h, s, false);
+  note_eig(td);
+  if (!td) sweeps = sym_eig_refined(G, n, V, h, max_sweeps, s);
+  return true;
+}
+
+}  // namespace
+
+int64_t mixed_bonds_kept() { return g_mixed_kept.load(); }
+int64_t mixed_bonds_escalated() { return g_mixed_escalated.load(); }
+
+namespace {
+
+// Direct route: one-sided Jacobi (through TSQR for tall-skinny shapes) on the
+// tall orientation of Z, FP64 whatever the precision.
+void svd_direct(const double* Z, int64_t M, int64_t N,
+                const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
+                SvdOut& out, cudaStream_t s) {
+  const bool tall = (M >= N);
+  const int64_t lg = tall ? M : N;
+  const int n = (int)(tall ? N : M);
+  DBuf<double> A((size_t)lg * n, s);   // column-major lg x n
+  if (tall) transpose_f64(Z, M, N, A.get(), s);  // columns of Z become contiguous
+  else FTT_CUDA(cudaMemcpyAsync(A.get(), Z, sizeof(double) * M * N, cudaMemcpyDeviceToDevice, s));
   DBuf<double> V((size_t)n * n, s);
   std::vector<double> h(n);
-  if (direct) {
-    identity_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(V.get(), n);
-    FTT_LAUNCH();
-    if (tsqr_applies(m_len, n) && lda == m_len) out.sweeps = tsqr_jacobi(A.get(), m_len, n, V.get(), max_sweeps, s);
-    else out.sweeps = jacobi_f64(A.get(), m_len, lda, n, V.get(), n, n, max_sweeps, s);
+  identity_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(V.get(), n);
+  FTT_LAUNCH();
+  if (tsqr_applies(lg, n)) out.sweeps = tsqr_jacobi(A.get(), lg, n, V.get(), max_sweeps, s);
+  else out.sweeps = jacobi_f64(A.get(), lg, lg, n, V.get(), n, n, max_sweeps, s);
+  {
     DBuf<double> norms(n, s);
-    col_norms_kernel<double><<<n, 256, 0, s>>>(A.get(), m_len, lda, n, norms.get());
+    col_norms_kernel<double><<<n, 256, 0, s>>>(A.get(), lg, lg, n, norms.get());
     FTT_LAUNCH();
     FTT_CUDA(cudaMemcpyAsync(h.data(), norms.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
-  } else {
-    const bool fast = sym_eig_fast(A.get(), n, V.get(), h, max_sweeps, s, mixed);
-    const bool td = fast || sym_eig_tridiag(A.get(), n, V.get(), h, s, mixed);
-    if (!fast) note_eig(td);
-    if (td) out.sweeps = 0;
-    else out.sweeps = mixed ? sym_eig_mixed32(A.get(), n, V.get(), h, max_sweeps, s)
-                            : sym_eig_refined(A.get(), n, V.get(), h, max_sweeps, s);
-    for (auto& x : h) x = sqrt(std::max(x, 0.0));  // eigenvalues of the Gram -> singular values
   }
   for (double x : h)
     if (!std::isfinite(x)) fail(FASTTT_ENUMERIC, "non-finite singular value");
+  // the column norms are the singular values: sort them as they are (squares would underflow)
   std::vector<int32_t> perm(n);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return h[a] > h[b]; });
@@ -1281,18 +1291,66 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
   FTT_CUDA(cudaMemcpyAsync(out.sigma.get(), sig.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
   out.U = DBuf<double>((size_t)M * r, s);
   out.Vt = DBuf<double>((size_t)r * N, s);
-  if (direct) {
-    if (tall) {  // Z V = A  ->  U = A Sigma^-1, Vt = V^T
-      gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(A.get(), lda, M, dperm.get(), dinv.get(), r, out.U.get());
-      FTT_LAUNCH();
-      gather_rows_kernel<<<grid_for(r * N), 256, 0, s>>>(V.get(), n, N, dperm.get(), nullptr, r, out.Vt.get());
-    } else {     // Z^T V = A  ->  Z = V Sigma (A Sigma^-1)^T
-      gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(V.get(), n, M, dperm.get(), nullptr, r, out.U.get());
-      FTT_LAUNCH();
-      gather_rows_kernel<<<grid_for(r * N), 256, 0, s>>>(A.get(), lda, N, dperm.get(), dinv.get(), r, out.Vt.get());
-    }
+  if (tall) {  // Z V = A  ->  U = A Sigma^-1, Vt = V^T
+    gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(A.get(), lg, M, dperm.get(), dinv.get(), r, out.U.get());
     FTT_LAUNCH();
-  } else if (tall) {  // V: right vectors; U = Z V_r Sigma^-1
+    gather_rows_kernel<<<grid_for(r * N), 256, 0, s>>>(V.get(), n, N, dperm.get(), nullptr, r, out.Vt.get());
+  } else {     // Z^T V = A  ->  Z = V Sigma (A Sigma^-1)^T
+    gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(V.get(), n, M, dperm.get(), nullptr, r, out.U.get());
+    FTT_LAUNCH();
+    gather_rows_kernel<<<grid_for(r * N), 256, 0, s>>>(A.get(), lg, N, dperm.get(), dinv.get(), r, out.Vt.get());
+  }
+  FTT_LAUNCH();
+  FTT_CUDA(cudaStreamSynchronize(s));   // host vectors read by the copies above
+}
+
+// Gram route at one precision level.  FP64 level (mixed = false) always completes.
+// Mixed: the Gram, the refinement and the projections are FP32-level products;
+// the result is kept only when (1) the probed distance of the FP32-level Gram from
+// Z^T Z (or Z Z^T) plus the refinement's rounding level gives an error floor that
+// the kept eigenvalues clear by kResolve and that cannot move the rank decision
+// (rank_is_resolved), and (2) the factor that the projection amplifies by
+// sigma_1 / sigma_r comes out of CholeskyQR2 orthonormal.  Otherwise false: the
+// caller redoes the bond at FP64 level.
+bool svd_gram(const double* Z, int64_t M, int64_t N,
+              const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
+              SvdOut& out, cudaStream_t s, bool mixed, int ortho, EigStart& st0) {
+  const bool tall = (M >= N);
+  const int n = (int)(tall ? N : M);
+  DBuf<double> A((size_t)n * n, s);
+  if (tall)  // G = Z^T Z
+    gemm(mixed, N, N, M, 1.0, Z, 1, N, Z, N, 1, 0.0, A.get(), N, 1, s, true);
+  else       // G = Z Z^T
+    gemm(mixed, M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, A.get(), M, 1, s, true);
+  DBuf<double> V((size_t)n * n, s);
+  std::vector<double> h(n);
+  int64_t sweeps = 0;
+  if (!gram_eig(A.get(), n, V.get(), h, max_sweeps, s, mixed, st0, sweeps)) return false;
+  out.sweeps = sweeps;
+  std::vector<int32_t> perm;
+  sigma_from_lambda(h, out.sigma_all, perm);
+  if (mixed) {
+    double lmax = 0.0;
+    for (double x : h) lmax = std::max(lmax, fabs(x));
+    const double floor = 4.0 * gram_error_probe(Z, M, N, A.get(), s) + 0x1p-21 * sqrt((double)n) * lmax;
+    if (!rank_is_resolved(choose_rank, out.sigma_all, n, floor)) return false;
+  }
+  A.reset();
+  int64_t r = choose_rank(out.sigma_all);
+  r = std::max<int64_t>(1, std::min<int64_t>(r, n));
+  out.r = r;
+  std::vector<double> sig(out.sigma_all.begin(), out.sigma_all.begin() + r), inv(r);
+  for (int64_t i = 0; i < r; ++i) inv[i] = sig[i] > 0.0 ? 1.0 / sig[i] : 0.0;
+  DBuf<int32_t> dperm(r, s);
+  DBuf<double> dinv(r, s);
+  out.sigma = DBuf<double>(r, s);
+  FTT_CUDA(cudaMemcpyAsync(dperm.get(), perm.data(), sizeof(int32_t) * r, cudaMemcpyHostToDevice, s));
+  FTT_CUDA(cudaMemcpyAsync(dinv.get(), inv.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  FTT_CUDA(cudaMemcpyAsync(out.sigma.get(), sig.data(), sizeof(double) * r, cudaMemcpyHostToDevice, s));
+  out.U = DBuf<double>((size_t)M * r, s);
+  out.Vt = DBuf<double>((size_t)r * N, s);
+  bool ok = true;
+  if (tall) {  // V: right vectors; U = Z V_r Sigma^-1
     DBuf<double> Vs((size_t)N * r, s);
     gather_cols_kernel<<<grid_for(N * r), 256, 0, s>>>(V.get(), n, N, dperm.get(), dinv.get(), r, Vs.get());
     FTT_LAUNCH();
@@ -1301,14 +1359,16 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
     gemm(mixed, M, r, N, 1.0, Z, N, 1, Vs.get(), r, 1, 0.0, out.U.get(), r, 1, s);
     if (mixed && ortho == kOrthoLeft) {
       // U = Z V Sigma^-1 carries the FP32-level product error times sigma_1 / sigma_r:
-      // make U orthonormal again and take Vt = Sigma^-1 U^T Z (U Sigma Vt = U U^T Z)
-      orthonormalise_cols_tc(out.U.get(), M, r, s);
-      DBuf<double> Us((size_t)M * r, s);
-      scale_cols_kernel2<<<grid_for(M * r), 256, 0, s>>>(out.U.get(), M, r, dinv.get(), Us.get());
-      FTT_LAUNCH();
-      gemm(mixed, r, N, M, 1.0, Us.get(), 1, r, Z, N, 1, 0.0, out.Vt.get(), N, 1, s);
+      // CholeskyQR2 makes U orthonormal, then Vt = Sigma^-1 U^T Z (U Sigma Vt = U U^T Z)
+      ok = orthonormalise_cols_cholqr2(out.U.get(), M, r, true, s);
+      if (ok) {
+        DBuf<double> Us((size_t)M * r, s);
+        scale_cols_kernel2<<<grid_for(M * r), 256, 0, s>>>(out.U.get(), M, r, dinv.get(), Us.get());
+        FTT_LAUNCH();
+        gemm(mixed, r, N, M, 1.0, Us.get(), 1, r, Z, N, 1, 0.0, out.Vt.get(), N, 1, s);
+      }
     }
-  } else {            // V: left vectors; Vt = Sigma^-1 U_r^T Z
+  } else {     // V: left vectors; Vt = Sigma^-1 U_r^T Z
     gather_cols_kernel<<<grid_for(M * r), 256, 0, s>>>(V.get(), n, M, dperm.get(), nullptr, r, out.U.get());
     FTT_LAUNCH();
     DBuf<double> Us((size_t)M * r, s);
@@ -1316,18 +1376,46 @@ void svd_truncated(const double* Z, int64_t M, int64_t N,
     FTT_LAUNCH();
     gemm(mixed, r, N, M, 1.0, Us.get(), 1, r, Z, N, 1, 0.0, out.Vt.get(), N, 1, s);
     if (mixed && ortho == kOrthoRight) {
-      // Vt = Sigma^-1 U^T Z: make its rows orthonormal again (columns of Vt^T) and take
-      // U = Z Vt^T Sigma^-1, so that U Sigma Vt = Z Vt^T Vt
-      DBuf<double> Vc((size_t)N * r, s);
-      transpose_f64(out.Vt.get(), r, N, Vc.get(), s);
-      orthonormalise_cols_tc(Vc.get(), N, r, s);
-      transpose_f64(Vc.get(), N, r, out.Vt.get(), s);
-      DBuf<double> ZV((size_t)M * r, s);
-      gemm(mixed, M, r, N, 1.0, Z, N, 1, Vc.get(), r, 1, 0.0, ZV.get(), r, 1, s);
-      scale_cols_kernel2<<<grid_for(M * r), 256, 0, s>>>(ZV.get(), M, r, dinv.get(), out.U.get());
-      FTT_LAUNCH();
+      // Vt = Sigma^-1 U^T Z: CholeskyQR2 on its rows, then U = Z Vt^T Sigma^-1, so that
+      // U Sigma Vt = Z Vt^T Vt
+      ok = cholqr2_rows(out.Vt.get(), r, N, nullptr, true, s);
+      if (ok) {
+        DBuf<double> ZV((size_t)M * r, s);
+        gemm(mixed, M, r, N, 1.0, Z, N, 1, out.Vt.get(), 1, N, 0.0, ZV.get(), r, 1, s);
+        scale_cols_kernel2<<<grid_for(M * r), 256, 0, s>>>(ZV.get(), M, r, dinv.get(), out.U.get());
+        FTT_LAUNCH();
+      }
     }
   }
+  FTT_CUDA(cudaStreamSynchronize(s));   // host vectors read by the copies above
+  return ok;
+}
+
+}  // namespace
+
+void svd_truncated(const double* Z, int64_t M, int64_t N,
+                   const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
+                   SvdOut& out, cudaStream_t s, bool mixed, int ortho) {
+  const bool tall = (M >= N);
+  const int64_t sm = tall ? N : M;   // number of singular values
+  const int64_t lg = tall ? M : N;
+  if (sm > INT32_MAX / 2) fail(FASTTT_ERANK, "SVD too large");
+  // direct (accurate) route while a Jacobi sweep stays below ~4e10 flops
+  const bool direct = (sm <= kDirectMax) || (9.0 * (double)lg * (double)sm * (double)sm <= 4.0e10);
+  if (direct) {
+    svd_direct(Z, M, N, choose_rank, max_sweeps, out, s);
+    return;
+  }
+  EigStart st0;
+  if (mixed) {
+    if (svd_gram(Z, M, N, choose_rank, max_sweeps, out, s, true, ortho, st0)) {
+      g_mixed_kept.fetch_add(1);
+      return;
+    }
+    g_mixed_escalated.fetch_add(1);
+    out = SvdOut();
+  }
+  svd_gram(Z, M, N, choose_rank, max_sweeps, out, s, false, ortho, st0);
 }
 
 bool sym_eig_fast(const double* G, int n, double* V, std::vector<double>& lam_out, int64_t max_sweeps, cudaStream_t s,
@@ -1348,24 +1436,32 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
                    SvdOut& out, cudaStream_t s, bool mixed) {
   if (M > INT32_MAX / 2) fail(FASTTT_ERANK, "SVD too large");
   const int n = (int)M;
+  const int nsv = (int)std::min<int64_t>(n, N);
   DBuf<double> V((size_t)n * n, s);
   std::vector<double> h(n);
-  const bool fast = sym_eig_fast(Gram, n, V.get(), h, max_sweeps, s, mixed);
-  const bool td = fast || sym_eig_tridiag(Gram, n, V.get(), h, s, mixed);
-  if (!fast) note_eig(td);
-  if (td) out.sweeps = 0;
-  else out.sweeps = mixed ? sym_eig_mixed32(Gram, n, V.get(), h, max_sweeps, s)
-                          : sym_eig_refined(Gram, n, V.get(), h, max_sweeps, s);
-  for (auto& x : h) {
-    x = sqrt(std::max(x, 0.0));
-    if (!std::isfinite(x)) fail(FASTTT_ENUMERIC, "non-finite singular value");
+  std::vector<int32_t> perm;
+  EigStart st0;
+  bool done = false;
+  if (mixed) {
+    // The Gram is an FP64 sum here: the error floor is the FP32-level refinement's
+    int64_t sw = 0;
+    if (gram_eig(Gram, n, V.get(), h, max_sweeps, s, true, st0, sw)) {
+      sigma_from_lambda(h, out.sigma_all, perm);
+      double lmax = 0.0;
+      for (double x : h) lmax = std::max(lmax, fabs(x));
+      out.sigma_all.resize(nsv);
+      done = rank_is_resolved(choose_rank, out.sigma_all, nsv, 0x1p-21 * sqrt((double)n) * lmax);
+      out.sweeps = sw;
+    }
+    (done ? g_mixed_kept : g_mixed_escalated).fetch_add(1);
   }
-  std::vector<int32_t> perm(n);
-  std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return h[a] > h[b]; });
-  const int nsv = (int)std::min<int64_t>(n, N);
-  out.sigma_all.resize(nsv);
-  for (int i = 0; i < nsv; ++i) out.sigma_all[i] = h[perm[i]];
+  if (!done) {
+    int64_t sw = 0;
+    gram_eig(Gram, n, V.get(), h, max_sweeps, s, false, st0, sw);
+    out.sweeps = sw;
+    sigma_from_lambda(h, out.sigma_all, perm);
+    out.sigma_all.resize(nsv);
+  }
   int64_t r = choose_rank(out.sigma_all);
   r = std::max<int64_t>(1, std::min<int64_t>(r, nsv));
   out.r = r;
@@ -1378,5 +1474,6 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
   FTT_LAUNCH();
   FTT_CUDA(cudaStreamSynchronize(s));   // perm and sigma_all are host memory read by the copies above
 }
+
 
 }  // namespace fasttt

@@ -131,4 +131,45 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
                    const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
                    SvdOut& out, cudaStream_t s, bool mixed = false);
 
+// ---------------------------------------------------------------- chol.cu
+
+// Upper Cholesky factor of the symmetric n x n row-major H in place (H = R^T R,
+// strict lower triangle zeroed), FP64 with FP64-level GEMM updates.  False when
+// a pivot is not above tiny_rel * max_i H_ii (or not finite).
+bool cholesky_upper(double* H, int64_t n, double tiny_rel, cudaStream_t s);
+
+// R^T X = B in place for the n x n upper R (row-major) and B (n rows x ncols,
+// row stride ldb), by substitution (recursive; the off-diagonal updates are
+// GEMMs, FP32-level when mixed).
+void trsm_upper_t(const double* R, int64_t n, double* B, int64_t ldb, int64_t ncols, bool mixed, cudaStream_t s);
+
+// V (n x n row-major) <- I.
+void identity_f64(double* V, int64_t n, cudaStream_t s);
+
+// Gram-route bonds of the mixed precision that kept their FP32-level result, and
+// those redone with FP64-level products, since the library was loaded.
+int64_t mixed_bonds_kept();
+int64_t mixed_bonds_escalated();
+
+// ||H - I||_F of the n x n row-major H.
+double identity_deviation(const double* H, int64_t n, cudaStream_t s);
+
+// CholeskyQR2 of the rows of Z (M x N row-major, M <= N): Z <- Q with orthonormal
+// rows and, when R is not null, R (M x M row-major upper) with Z_in = R^T Q.  The
+// Grams and the solve updates are FP32-level products when mixed; the Cholesky
+// factorisations and R = R2 R1 are FP64.  False (Z undefined) on a Cholesky
+// breakdown or when the second Gram is further than 0.5 from I (Z too ill
+// conditioned for the Gram's precision); dev_out gets that distance.
+bool cholqr2_rows(double* Z, int64_t M, int64_t N, double* R, bool mixed, cudaStream_t s, double* dev_out = nullptr);
+
+// The columns of the row-major rows x r matrix U made orthonormal by CholeskyQR2
+// (through its transpose); false as cholqr2_rows.
+bool orthonormalise_cols_cholqr2(double* U, int64_t rows, int64_t r, bool mixed, cudaStream_t s);
+
+// Estimate of ||G~ - G||_F for a Gram G~ of Z (Z^T Z when M >= N, else Z Z^T)
+// that was formed with FP32-level products: the mean of ||(G~ - G) x||^2 over
+// four +-1 probe vectors x (an unbiased estimate of the squared Frobenius norm),
+// G x taken as Z^T (Z x) or Z (Z^T x) in FP64.
+double gram_error_probe(const double* Z, int64_t M, int64_t N, const double* G, cudaStream_t s);
+
 }  // namespace fasttt

@@ -316,10 +316,11 @@ void finish_stats(fasttt_stats& st, int64_t launches0) {
 }
 
 struct CounterSnap {
-  int64_t block_sweeps, eig_tridiag, eig_fallback, eig_fast;
+  int64_t block_sweeps, eig_tridiag, eig_fallback, eig_fast, mixed_kept, mixed_esc;
 };
 CounterSnap counter_snap() {
-  return {block_sweep_count(), g_eig_tridiag.load(), g_eig_fallback.load(), g_eig_fast.load()};
+  return {block_sweep_count(), g_eig_tridiag.load(), g_eig_fallback.load(), g_eig_fast.load(),
+          mixed_bonds_kept(), mixed_bonds_escalated()};
 }
 void finish_block_stats(fasttt_stats& st, const CounterSnap& c0) {
   st.jacobi_block_sweeps = block_sweep_count() - c0.block_sweeps;
@@ -327,12 +328,37 @@ void finish_block_stats(fasttt_stats& st, const CounterSnap& c0) {
   st.eig_tridiag = g_eig_tridiag.load() - c0.eig_tridiag;
   st.eig_fallbacks = g_eig_fallback.load() - c0.eig_fallback;
   st.eig_fast = g_eig_fast.load() - c0.eig_fast;
+  st.mixed_fp32_bonds = mixed_bonds_kept() - c0.mixed_kept;
+  st.mixed_fp64_bonds = mixed_bonds_escalated() - c0.mixed_esc;
 }
 
 double tail2(const std::vector<double>& s, int64_t r) {
   double acc = 0.0;
   for (int64_t i = (int64_t)s.size() - 1; i >= r; --i) acc += s[i] * s[i];
   return acc;
+}
+
+// QR step of Alg. 6's right-to-left sweep for Z = unfold_1(G_k) (M x N, N = n_k r_k):
+// Z = R^T Q with Q's rows orthonormal.  M <= N: CholeskyQR2 of Z's rows (G_k <- Q,
+// US <- R^T, q = M); false, G_k untouched, when it breaks down (the caller takes
+// an untruncated SVD).  M > N: Q = I (G_k <- the N x N identity, US <- Z, q = N),
+// which is exact.
+bool qr_factor(DBuf<double>& Gk, int64_t M, int64_t N, bool mixed, DBuf<double>& US, int64_t& q, cudaStream_t s) {
+  if (M > N) {
+    US = std::move(Gk);
+    Gk = DBuf<double>((size_t)N * N, s);
+    identity_f64(Gk.get(), N, s);
+    q = N;
+    return true;
+  }
+  DBuf<double> Z((size_t)M * N, s), R((size_t)M * M, s);
+  FTT_CUDA(cudaMemcpyAsync(Z.get(), Gk.get(), Z.bytes(), cudaMemcpyDeviceToDevice, s));
+  if (!cholqr2_rows(Z.get(), M, N, R.get(), mixed, s)) return false;
+  Gk = std::move(Z);
+  US = DBuf<double>((size_t)M * M, s);
+  transpose_f64(R.get(), M, M, US.get(), s);
+  q = M;
+  return true;
 }
 
 void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const void* d_vals, int val_dtype,
@@ -424,8 +450,11 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
     return X;
   };
   double err2 = 0.0;
+  std::vector<double> kappa(d + 1, 0.0);   // sigma_1 / sigma_r of the kept values per bond
   auto record = [&](int bond, const SvdOut& sv, double dl) {
     const double e2 = tail2(sv.sigma_all, sv.r);
+    if (sv.r > 0 && sv.r <= (int64_t)sv.sigma_all.size() && sv.sigma_all[sv.r - 1] > 0.0)
+      kappa[bond] = sv.sigma_all[0] / sv.sigma_all[sv.r - 1];
     err2 += e2;
     st.deltas[bond] = dl;
     st.jacobi_sweeps += sv.sweeps;
@@ -546,15 +575,27 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
     // unfold_1(G_k) = U S V^T (Q = V, R = S U^T); G_{k-1} := G_{k-1} x_3 R^T
     for (int k = d; k >= p + 1; --k) {
       const int64_t M = r[k - 1], N = n[k - 1] * r[k];
-      SvdOut sv;
-      svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) { return (int64_t)sg.size(); },
-                    max_sweeps, sv, s, mixed, 2);
-      st.jacobi_sweeps += sv.sweeps;
-      const int64_t q = sv.r;
-      G[k] = std::move(sv.Vt);
-      DBuf<double> US((size_t)M * q, s);
-      scale_cols_kernel<<<grid_for(M * q), 256, 0, s>>>(sv.U.get(), M, q, sv.sigma.get(), US.get());
-      FTT_LAUNCH();
+      int64_t q = 0;
+      DBuf<double> US;
+      // FP32-level CholeskyQR2 only where bond k-1's kept singular values (those of
+      // unfold_1(G_k) while everything right of it is orthonormal) span less than
+      // 2^-6 of the FP32 level's u^{-1/2}; FP64-level otherwise
+      const double kap = kappa[k - 1];
+      const bool qr_mixed = mixed && kap > 0.0 && std::isfinite(kap) && kap * kap * 0x1p-23 < 0x1p-6;
+      if (qr_factor(G[k], M, N, qr_mixed, US, q, s)) {
+        ++st.qr_cholqr2;
+      } else {
+        SvdOut sv;
+        svd_truncated(G[k].get(), M, N, [&](const std::vector<double>& sg) { return (int64_t)sg.size(); },
+                      max_sweeps, sv, s, mixed, 2);
+        st.jacobi_sweeps += sv.sweeps;
+        q = sv.r;
+        G[k] = std::move(sv.Vt);
+        US = DBuf<double>((size_t)M * q, s);
+        scale_cols_kernel<<<grid_for(M * q), 256, 0, s>>>(sv.U.get(), M, q, sv.sigma.get(), US.get());
+        FTT_LAUNCH();
+        ++st.qr_svd;
+      }
       if (k - 1 == p && UC.get()) {
         // G_p = Q_S UC:  G_p R^T = Q_S (UC R^T), a beta_r-row GEMM, then one expansion
         const int64_t br = dp.rows.beta;
@@ -1098,6 +1139,22 @@ int fasttt_debug_svd(int64_t M, int64_t N, const double* d_Z, double* h_sigma, d
     FTT_CUDA(cudaStreamSynchronize(s));
     ozaki_take_timeout(s);
     std::copy(sv.sigma_all.begin(), sv.sigma_all.begin() + r, h_sigma);
+    return FASTTT_OK;
+  } catch (const Error& e) {
+    return handle_error(e);
+  }
+}
+
+int fasttt_debug_cholqr(int64_t M, int64_t N, double* d_Z, double* d_R, int precision, void* stream) {
+  try {
+    if (M < 1 || N < M || !d_Z || !d_R || (precision != FASTTT_PREC_FP64 && precision != FASTTT_PREC_MIXED))
+      fail(FASTTT_EINVAL, "fasttt_debug_cholqr: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    set_gemm_engine(FASTTT_GEMM_TENSOR);
+    const bool ok = cholqr2_rows(d_Z, M, N, d_R, precision == FASTTT_PREC_MIXED, s);
+    FTT_CUDA(cudaStreamSynchronize(s));
+    ozaki_take_timeout(s);
+    if (!ok) fail(FASTTT_ENUMERIC, "CholeskyQR2 broke down (matrix too ill conditioned for the Gram's precision)");
     return FASTTT_OK;
   } catch (const Error& e) {
     return handle_error(e);

@@ -45,7 +45,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("rounding", ctypes.c_int),
                 ("depar_values", ctypes.c_int), ("stage", ctypes.c_int), ("keep_intermediates", ctypes.c_int),
                 ("max_rank", ctypes.c_int64), ("max_sweeps", ctypes.c_int64), ("sparse_sweep", ctypes.c_int),
-                ("gemm_engine", ctypes.c_int)]
+                ("gemm_engine", ctypes.c_int), ("max_spin", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -67,7 +67,9 @@ class Stats(ctypes.Structure):
                 ("eig_tridiag", ctypes.c_int64), ("eig_fallbacks", ctypes.c_int64),
                 ("ms_gemm_oz", ctypes.c_double), ("flop_gemm_oz", ctypes.c_double),
                 ("ms_tridiag32", ctypes.c_double), ("flop_tridiag32", ctypes.c_double),
-                ("ms_tsqr", ctypes.c_double), ("flop_tsqr", ctypes.c_double), ("eig_fast", ctypes.c_int64)]
+                ("ms_tsqr", ctypes.c_double), ("flop_tsqr", ctypes.c_double), ("eig_fast", ctypes.c_int64),
+                ("qr_cholqr2", ctypes.c_int64), ("qr_svd", ctypes.c_int64), ("mixed_fp32_bonds", ctypes.c_int64),
+                ("mixed_fp64_bonds", ctypes.c_int64)]
 
     def to_dict(self):
         d = self.d
@@ -89,7 +91,8 @@ class Stats(ctypes.Structure):
                 "eig_fallbacks": self.eig_fallbacks, "ms_gemm_oz": self.ms_gemm_oz,
                 "flop_gemm_oz": self.flop_gemm_oz, "ms_tridiag32": self.ms_tridiag32,
                 "flop_tridiag32": self.flop_tridiag32, "ms_tsqr": self.ms_tsqr, "flop_tsqr": self.flop_tsqr,
-                "eig_fast": self.eig_fast}
+                "eig_fast": self.eig_fast, "qr_cholqr2": self.qr_cholqr2, "qr_svd": self.qr_svd,
+                "mixed_fp32_bonds": self.mixed_fp32_bonds, "mixed_fp64_bonds": self.mixed_fp64_bonds}
 
 
 _P = ctypes.c_void_p
@@ -129,6 +132,7 @@ _lib.fasttt_version.restype = ctypes.c_char_p
 _lib.fasttt_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
 _lib.fasttt_debug_sym_eig.argtypes = [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, _P]
 _lib.fasttt_debug_gemm.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _P]
+_lib.fasttt_debug_cholqr.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, ctypes.c_int, _P]
 _lib.fasttt_debug_gram.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, _P, ctypes.c_int, _P]
 _lib.fasttt_debug_svd.argtypes = [ctypes.c_int64, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), _P, _P,
                                   ctypes.c_int, _P]
@@ -137,7 +141,7 @@ EXPORTS = ["fasttt_default_opts", "fasttt_decompose", "fasttt_tt_free", "fasttt_
            "fasttt_tt_core", "fasttt_tt_count", "fasttt_tt_copy", "tt_eval_at", "tt_eval_backward",
            "tt_eval_backward_noalloc",
            "fasttt_last_error", "fasttt_version", "fasttt_debug_fail_alloc_after", "fasttt_debug_sym_eig",
-           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_svd", "fasttt_tt_round", "fasttt_tt_add", "tt_fit_gd",
+           "fasttt_debug_gemm", "fasttt_debug_gram", "fasttt_debug_cholqr", "fasttt_debug_svd", "fasttt_tt_round", "fasttt_tt_add", "tt_fit_gd",
            "fasttt_debug_select_p", "fasttt_debug_rank_rule"]
 
 
@@ -235,6 +239,21 @@ def debug_svd(Z, precision="fp64", stream=None):
                                ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(Vt.data_ptr()), prec, _stream(stream))
     _check(rc)
     return sigma, U, Vt
+
+
+def debug_cholqr(Z, precision="fp64", stream=None):
+    """CholeskyQR2 of the rows of an FP64 CUDA matrix Z (M x N, M <= N) through the library
+    (a test hook).  Returns (Q (M, N) torch with orthonormal rows, R (M, M) torch upper) with Z = R^T Q."""
+    _require_cuda()
+    Q = _dev(Z, torch.float64).clone()
+    M, N = Q.shape
+    if precision not in ("fp64", "mixed"):
+        raise FastTTError(EINVAL, "precision must be 'fp64' or 'mixed'")
+    R = torch.empty((M, M), dtype=torch.float64, device=Q.device)
+    rc = _lib.fasttt_debug_cholqr(M, N, ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(R.data_ptr()),
+                                  PREC_FP64 if precision == "fp64" else PREC_MIXED, _stream(stream))
+    _check(rc)
+    return Q, R
 
 
 def debug_gram(A, engine, stream=None):

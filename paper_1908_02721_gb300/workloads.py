@@ -268,3 +268,15 @@ def random_tt(dims, ranks, seed: int, decay: float = 1.0):
             G = G * (decay ** np.arange(ranks[k + 1]))[None, None, :]
         cores.append(G)
     return cores
+
+
+def sample_positions(w: Workload, n_nonzero: int, n_uniform: int, seed: int) -> np.ndarray:
+    """Positions at which two TTs of the workload's shape are compared entry by
+    entry: ``n_nonzero`` of the workload's nonzero coordinates (drawn without
+    replacement) followed by ``n_uniform`` uniform coordinates of the whole
+    index space.  (d, n_nonzero + n_uniform) int32."""
+    rng = _rng(seed)
+    pick = rng.choice(w.nnz, size=min(n_nonzero, w.nnz), replace=False)
+    uni = np.stack([rng.integers(0, n, size=n_uniform) for n in w.dims]) if n_uniform else \
+        np.zeros((w.d, 0), dtype=np.int64)
+    return np.ascontiguousarray(np.concatenate([w.idx[:, pick].astype(np.int64), uni], axis=1).astype(np.int32))

@@ -68,11 +68,13 @@ def test_struct_field_order_matches_header(lib):
 
 def test_struct_layouts_match_header(lib):
     from paper_1908_02721_gb300 import fasttt as F
-    # fasttt_opts: six ints, two int64, two ints; fasttt_stats ends with the kernel-class doubles
-    assert ctypes.sizeof(F.Opts) == 8 * 4 + 2 * 8
+    # fasttt_opts: six ints, two int64, two ints, one int64; fasttt_stats ends with the
+    # route counters (int64)
+    assert ctypes.sizeof(F.Opts) == 8 * 4 + 3 * 8
     assert F.Opts.sparse_sweep.offset == 6 * 4 + 2 * 8
+    assert F.Opts.max_spin.offset == 8 * 4 + 2 * 8
     assert F.Stats.flop_gemm_oz.offset + 8 == F.Stats.ms_tridiag32.offset
-    assert F.Stats.eig_fast.offset + 8 == ctypes.sizeof(F.Stats)
+    assert F.Stats.mixed_fp64_bonds.offset + 8 == ctypes.sizeof(F.Stats)
 
 
 def test_calls_without_gpu_fail_loudly(lib):

@@ -394,25 +394,3 @@ def test_uniform5_full_size_properties(F):
     tt.free()
 
 
-# ---------------------------------------------------------------- E1: mixed precision
-
-MIXED_TOL = 1e-5
-
-
-@pytest.mark.parametrize("name", ["uniform5-n30", "qtt-m10"])
-def test_mixed_precision_against_fp64_oracle(F, name):
-    """Mixed precision (split-TF32 tensor-core GEMMs, FP32 Jacobi, FP64 rank rule): ranks equal
-    to the FP64 oracle's where the spectra are well resolved, products within 1e-5 relative."""
-    w = W.uniform5(seed=2, nnz=7776, n=30) if name == "uniform5-n30" else W.banded_qtt(10)
-    tt = F.fasttt_decompose(w.idx, w.vals, w.dims, w.eps, precision="mixed")
-    res = O.fasttt(w.idx, w.vals, w.dims, w.eps)
-    assert tt.stats["p"] == res.p
-    nA = math.sqrt(res.norm2)
-    diff = D.tt_diff_norm(_cores_np(tt), res.cores)
-    assert diff <= MIXED_TOL * nA, diff / nA
-    if name == "uniform5-n30":
-        assert tt.ranks == res.ranks
-        assert tt.stats["ms_gemm_tc"] > 0.0        # the tensor-core GEMMs ran
-    else:   # ranks may differ only where singular values sit at the FP32 noise level
-        assert all(abs(a - b) <= 0.02 * max(a, b) for a, b in zip(tt.ranks, res.ranks))
-    tt.free()
