@@ -394,3 +394,34 @@ def test_uniform5_full_size_properties(F):
     tt.free()
 
 
+
+
+# ---------------------------------------------------------------- Alg. 8 on the hand-worked input
+
+def _read_alg8_golden():
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "alg8_example.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+@pytest.mark.parametrize("row", _read_alg8_golden())
+def test_alg8_hand_worked_on_gpu(F, row):
+    """Alg. 8 (and the static schedule) on the superdiagonal tensor whose ranks were
+    derived by hand (tests/golden/alg8_example.txt): ranks and err2 exact, products
+    within 1e-12 of the oracle's."""
+    s = np.array([8.0, 4.0, 2.0, 1.0, 0.5])
+    idx = np.tile(np.arange(5, dtype=np.int32), (4, 1))
+    dims = [5, 5, 5, 5]
+    eps = 1.2 / math.sqrt(float(np.sum(s * s)))
+    p, rounding = int(row[0]), row[1]
+    tt = F.fasttt_decompose(idx, s, dims, eps, p=p, rounding=rounding)
+    assert tt.ranks == [int(x) for x in row[2:7]]
+    assert abs(tt.stats["err2"] - float(row[7])) <= 1e-12
+    res = O.fasttt(idx, s, dims, eps, p=p, rounding=rounding)
+    assert D.tt_diff_norm(_cores_np(tt), res.cores) <= TOL * math.sqrt(res.norm2)
+    tt.free()

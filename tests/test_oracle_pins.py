@@ -230,6 +230,30 @@ def test_dynamic_alg8_bound():
             assert sum(dy.ranks) <= sum(st.ranks) + 2 * w.d
 
 
+def superdiagonal_alg8_workload():
+    """The hand-worked Alg. 8 input of tests/golden/alg8_example.txt: 4 modes of size
+    5, A(i,i,i,i) = (8, 4, 2, 1, 1/2)_i, eps ||A|| = 1.2."""
+    s = np.array([8.0, 4.0, 2.0, 1.0, 0.5])
+    idx = np.tile(np.arange(5, dtype=np.int32), (4, 1))
+    return idx, s, [5, 5, 5, 5], 1.2 / math.sqrt(float(np.sum(s * s)))
+
+
+@pytest.mark.parametrize("row", _read_golden("alg8_example.txt"))
+def test_alg8_hand_worked_ranks(row):
+    """Alg. 8 pinned by hand: delta_right / sqrt(d-k) (and delta_left / sqrt(k-1)) on a
+    superdiagonal tensor whose spectra are known in closed form.  The schedule
+    delta / (d-k), or the static eq. (11), gives other ranks on the same input."""
+    p, rounding = int(row[0]), row[1]
+    ranks = [int(x) for x in row[2:7]]
+    err2 = float(row[7])
+    idx, vals, dims, eps = superdiagonal_alg8_workload()
+    res = F.fasttt(idx, vals, dims, eps, p=p, rounding=rounding)
+    assert res.ranks == ranks
+    assert abs(res.err2 - err2) <= 1e-12
+    A = D.full_from_coo(idx, vals, dims)
+    assert abs(np.linalg.norm(A - D.tt_full(res.cores)) ** 2 - err2) <= 1e-12
+
+
 # ---------------------------------------------------------------- value Depar (S6)
 
 def test_value_depar_factorisation_and_planted_parallels():
