@@ -1,12 +1,22 @@
 """FastTT throughput on one GB300 (nnz/s), one JSON line on stdout.
 
-Workload (default): 5-way 50^5 sparse tensor, 1e5 distinct uniform positions,
-N(0,1) values, eps = 1e-8, plain FastTT in FP64 (grouping, value Depar, dense
-middle TT-SVD, TT-rounding).  A step is one fasttt_decompose over the whole
-tensor.  `value` is device-resident throughput (inputs already in HBM);
-`e2e` runs the same call from pinned host buffers with the host->device copy of
-the COO input and the device->host copy of every output core inside the timed
-region.
+Headline workload: the banded sparse matrix of the sparse-matrix -> QTT
+configuration at 2^12 x 2^12 (5-diagonal band + 5 uniform off-band entries per
+row, U(-1,1), row/column bits interleaved into 12 modes of size 4), eps = 1e-6:
+the FP64-vs-mixed comparison at relative error <= 1e-6.  The full 2^20 x 2^20
+matrix has exact TT ranks near 1e6 and cannot be rounded densely on one GPU; its
+grouping (S1-S5) is timed at full size as a secondary line.  A step is one
+fasttt_decompose over the whole tensor.  `value` is the FP64 path's
+device-resident throughput (the path whose sampled error meets 1e-6); the mixed
+path is timed the same way beside it.  `e2e` runs the same call from pinned host
+buffers with the host->device copy of the COO input and the device->host copy of
+every output core inside the timed region.
+
+Secondary lines (each timed after the headline, guarded): the 5-way 50^5 tensor
+(1e5 nnz, eps 1e-8), the Zipf 8-way 100^8 tensor (1e7 nnz, FP32 values, eps 1e-4,
+rank cap 64) and the clustered 12-way 64^12 tensor (5e7 nnz, eps 1e-5, rank cap
+128), each in FP64 and mixed precision; entry evaluation + adjoint; TT-rounding;
+fitting; dynamic truncation; the FDM matrices of Table 2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,8 +40,10 @@ sys.path.insert(0, ROOT)
 METRIC = "FastTT nnz/s at rel. err <=1e-6 (FP64 vs mixed, 1 GB300); adjoint % HBM roofline"
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
 FP32_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12  # 128 FFMA/clk/SM x 152 SMs x 2070 MHz
-SAMPLE_N = 30                                       # oracle sample: same recipe at mode size 30
+HEADLINE_M = 12                                     # 2^12 x 2^12 banded matrix, 12 modes of size 4
+SAMPLE_M = 10                                       # oracle sample: the same recipe at 2^10 x 2^10
 OZ_PAIRS_FP64 = 36                                  # slice pairs (s, t), s + t <= 9, of the 8-slice product
+ERR_BAR = 1e-6                                      # the metric's relative-error bar
 
 
 def _peaks():
@@ -98,18 +110,17 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _workload(rank, name="uniform5"):
+def _workload(rank, name="qtt12"):
     from paper_1908_02721_gb300 import workloads as W
-    if name == "uniform5-n30":   # small case of the same recipe (profiling captures)
-        return W.uniform5(seed=2 + 1000 * rank, nnz=int(round(100_000 * (SAMPLE_N / 50) ** 5)), n=SAMPLE_N)
-    return W.uniform5(seed=2 + 1000 * rank)
+    if name == "qtt10":   # small case of the same recipe (profiling captures)
+        return W.banded_qtt(SAMPLE_M, seed=3 + 1000 * rank, eps=1e-6)
+    return W.banded_qtt(HEADLINE_M, seed=3 + 1000 * rank, eps=1e-6)
 
 
 def _sample_workload():
-    """The oracle's bounded sample: the same recipe at mode size 30 (same density)."""
+    """The oracle's bounded sample: the same recipe at 2^10 x 2^10 (10 modes of size 4)."""
     from paper_1908_02721_gb300 import workloads as W
-    nnz = int(round(100_000 * (SAMPLE_N / 50) ** 5))
-    return W.uniform5(seed=2, nnz=nnz, n=SAMPLE_N)
+    return W.banded_qtt(SAMPLE_M, seed=3, eps=1e-6)
 
 
 def _oracle_step(w):
@@ -138,6 +149,10 @@ def _cores():
         return os.cpu_count()
 
 
+HEADLINE_NAME = (f"banded sparse matrix -> QTT: 2^{HEADLINE_M} x 2^{HEADLINE_M}, band5 + 5 off-band per row, "
+                 f"U(-1,1), {HEADLINE_M} modes of size 4, eps=1e-6")
+
+
 def run_reference(args):
     world, rank = _dist()
     if rank != 0:
@@ -148,16 +163,43 @@ def run_reference(args):
     ts = [_oracle_step(w) for _ in range(args.steps)]
     total = sum(ts)
     value = w.nnz * args.steps / total
+    sample = (f"FP64 oracle, full FastTT per step on the same recipe at 2^{SAMPLE_M} x 2^{SAMPLE_M} "
+              f"({SAMPLE_M} modes of size 4, {w.nnz} nnz, eps=1e-6); the 2^{HEADLINE_M} case takes about "
+              "10 minutes per run, beyond a bounded step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"FP64 CPU oracle on a bounded sample: 5-way {SAMPLE_N}^5, {w.nnz} nnz, "
-                                   "N(0,1), eps=1e-8 (same recipe and density as the 50^5, 1e5-nnz workload)"},
-            "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": _cores(), "kind": "oracle",
-                             "sample": f"5-way {SAMPLE_N}^5, {w.nnz} nnz, full FastTT per step"},
+            "config": {"workload": HEADLINE_NAME, "sample": sample, "same_config": False},
+            "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": _cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _time_steps(F, idx, vals, w, steps, warmup, flush, stream, **kw):
+    """Warm-up calls, then `steps` timed decompositions (CUDA events on the launching
+    stream, L2 flushed between steps outside the events); the last handle is returned."""
+    import torch
+    for _ in range(warmup):
+        F.fasttt_decompose(idx, vals, w.dims, w.eps, max_rank=w.max_rank, **kw).free()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    tt, stats = None, []
+    for i in range(steps):
+        if tt is not None:
+            tt.free()
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        tt = F.fasttt_decompose(idx, vals, w.dims, w.eps, max_rank=w.max_rank, **kw)
+        ev[i][1].record(stream)
+        stats.append(tt.stats)
+    torch.cuda.synchronize()
+    return tt, stats, [a.elapsed_time(b) for a, b in ev]
+
+
+STAGE_KEYS = ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm_oz", "ms_gemm", "ms_jacobi", "ms_tsqr",
+              "ms_tridiag32", "ms_tridiag", "ms_tdeig", "ms_jacobi32", "ms_sort")
+ROUTE_KEYS = ("eig_fast", "eig_tridiag", "eig_fallbacks", "sparse_bonds", "qr_cholqr2", "qr_svd",
+              "mixed_fp32_bonds", "mixed_fp64_bonds")
 
 
 def run_ours(args):
@@ -209,15 +251,16 @@ def run_ours(args):
 
     # accuracy of the timed configuration: relative error of B at a fixed sample of nonzeros
     rel_err = _sampled_rel_err(F, idx, w, "fp64")
-    mixed_line = None if args.no_mixed else _mixed(args, F, idx, vals, w, flush, stream)
-    adjoint_line = None if args.no_adjoint else _adjoint(args, F, dev, stream)
-    round_line = None if args.no_tt_round else _tt_round(F, dev, stream)
+    mixed_line = None if args.no_mixed else _mixed(args, F, idx, vals, w, flush, stream, ms)
 
     # e2e through the same C-ABI call from pinned host memory
     e2e_line = None
     if not args.no_e2e:
         e2e_line = _e2e(args, w, F, dev, barrier, world)
-    # last: extension timings, each guarded (nothing after them depends on the device)
+    # the other configurations, then the extension timings, each guarded
+    configs_line = None if args.no_configs else _configs(args, F, dev, flush, stream, world)
+    adjoint_line = None if args.no_adjoint else _adjoint(args, F, dev, stream)
+    round_line = None if args.no_tt_round else _tt_round(F, dev, stream)
     next_line = None if args.no_tt_round else _next_rows(F, dev, stream)
     if adjoint_line is not None and "_fit_args" in adjoint_line:
         cores8, aidx, aw, am = adjoint_line.pop("_fit_args")
@@ -228,61 +271,69 @@ def run_ours(args):
         return
     st = stats[-1]
     peaks, src = _peaks()
-    # dominant kernel class by device time.  The tcgen05 GEMM computes an FP64 product from 8
-    # exact bf16 slices per operand: 36 slice-pair products, so its tensor-pipe work is
-    # 36 x 2MNK bf16 flops, measured against the bf16 dense peak -- the sustained one, as the
-    # slice GEMM's launches are spread over the whole step.
-    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1921.5))
-    classes = {"gemm_f64_kernel": (st["ms_gemm"], st["flop_gemm"], "alu", FP64_PEAK_TFLOPS),
-               "jacobi_sweep_kernel<double>": (st["ms_jacobi"], st["flop_jacobi"], "alu", FP64_PEAK_TFLOPS),
-               "tridiag_kernel": (st["ms_tridiag"], st["flop_tridiag"], "alu", FP64_PEAK_TFLOPS),
-               "ozaki_gemm_kernel<8,7,384,64,2>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor", bf16_peak),
-               "tridiag_kernel<float>": (st["ms_tridiag32"], st["flop_tridiag32"], "alu", FP32_PEAK_TFLOPS),
-               "qr_blocks_kernel+qr_apply_kernel": (st["ms_tsqr"], st["flop_tsqr"], "alu", FP64_PEAK_TFLOPS)}
-    name, (kms, kwork, bound, peak) = max(classes.items(), key=lambda kv: kv[1][0])
-    achieved = kwork / (kms / 1e3) / 1e12 if kms > 0 else 0.0
-    roofline = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": (("bf16 dense, measured, sustained (MEASURED_PEAKS.json bf16_tflops_sustained: the kernel's "
-                                 "launches run throughout the step)") if bound == "tensor" else
-                                "FP32 FFMA: 128 per clock per SM x 152 SMs x 2070 MHz (derived)" if peak == FP32_PEAK_TFLOPS else
-                                "FP64 DFMA: 2 per clock per SM x 152 SMs x 2070 MHz (derived; measured 1.198)"),
-                "share_of_step": kms / st["ms_total"] if st["ms_total"] else None}
-    if st["ms_gemm_oz"] > 0:
-        roofline["ozaki_fp64_equivalent_tflops"] = st["flop_gemm_oz"] / (st["ms_gemm_oz"] / 1e3) / 1e12
+    roofline = _roofline(st, peaks)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sw = _sample_workload()
         t = _oracle_step(sw)
         cpu = {"value": sw.nnz / t, "unit": "nnz/s", "cores": _cores(), "kind": "oracle",
-               "sample": f"FP64 oracle, full FastTT on the same recipe at 5-way {SAMPLE_N}^5 ({sw.nnz} nnz), one run"}
+               "sample": (f"FP64 oracle, full FastTT on the same recipe at 2^{SAMPLE_M} x 2^{SAMPLE_M} "
+                          f"({sw.nnz} nnz), one run")}
     line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": ("5-way 50^5, 1e5 distinct uniform positions, N(0,1), eps=1e-8, FP64 FastTT"
-                                    if args.workload == "uniform5" else f"profiling case {args.workload}"),
+            "config": {"workload": (HEADLINE_NAME + ", FP64 FastTT" if args.workload == "qtt12"
+                                    else f"profiling case {args.workload}"),
                        "nnz": w.nnz, "dims": w.dims, "eps": w.eps, "p": st["p"], "ranks": st["ranks"],
                        "rt": st["rt"], "beta": [st["beta_r"], st["beta_c"]],
                        "l2": "flushed between steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e_line,
             "rel_err_sampled": rel_err,
+            "meets_err_bar": rel_err <= ERR_BAR,
             "mixed": mixed_line,
+            "configs": configs_line,
             "adjoint": adjoint_line,
             "tt_round": round_line,
             "next_rows": next_line,
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
-            "stages_ms": {k: st[k] for k in ("ms_ingest", "ms_group", "ms_depar", "ms_round", "ms_gemm_oz", "ms_gemm",
-                                              "ms_jacobi", "ms_tsqr", "ms_tridiag32", "ms_tridiag", "ms_tdeig",
-                                              "ms_jacobi32", "ms_sort")},
-            "gram_eigensolver": {"fast": st["eig_fast"], "tridiagonal": st["eig_tridiag"],
-                                 "iterative_fallback": st["eig_fallbacks"]},
+            "stages_ms": {k: st[k] for k in STAGE_KEYS},
+            "routes": {k: st[k] for k in ROUTE_KEYS},
             "jacobi_sweeps": st["jacobi_sweeps"],
             "wall_s": wall, "peaks_source": src}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _roofline(st, peaks):
+    """The dominant kernel class of one step by CUDA-event time, its achieved rate against
+    its peak.  The tcgen05 GEMM computes an FP64 product from 8 exact bf16 slices per
+    operand: 36 slice-pair products, so its tensor-pipe work is 36 x 2MNK bf16 flops,
+    measured against the bf16 dense peak -- the sustained one, as the slice GEMM's launches
+    are spread over the whole step."""
+    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1921.5))
+    classes = {"gemm_f64_kernel": (st["ms_gemm"], st["flop_gemm"], "alu", FP64_PEAK_TFLOPS),
+               "jacobi_sweep_kernel<double>": (st["ms_jacobi"], st["flop_jacobi"], "alu", FP64_PEAK_TFLOPS),
+               "tridiag_kernel<double>": (st["ms_tridiag"], st["flop_tridiag"], "alu", FP64_PEAK_TFLOPS),
+               "ozaki_gemm_kernel<8,7,384,64,2>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor",
+                                                   bf16_peak),
+               "tridiag_kernel<float>": (st["ms_tridiag32"], st["flop_tridiag32"], "alu", FP32_PEAK_TFLOPS),
+               "qr_blocks_kernel+qr_apply_kernel": (st["ms_tsqr"], st["flop_tsqr"], "alu", FP64_PEAK_TFLOPS)}
+    name, (kms, kwork, bound, peak) = max(classes.items(), key=lambda kv: kv[1][0])
+    achieved = kwork / (kms / 1e3) / 1e12 if kms > 0 else 0.0
+    out = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
+           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+           "peak_source": (("bf16 dense, measured, sustained (MEASURED_PEAKS.json bf16_tflops_sustained: the kernel's "
+                            "launches run throughout the step)") if bound == "tensor" else
+                           "FP32 FFMA: 128 per clock per SM x 152 SMs x 2070 MHz (derived)" if peak == FP32_PEAK_TFLOPS
+                           else "FP64 DFMA: 2 per clock per SM x 152 SMs x 2070 MHz (derived; measured 1.198)"),
+           "share_of_step": kms / st["ms_total"] if st["ms_total"] else None,
+           "classes_ms": {k: v[0] for k, v in classes.items()}}
+    if st["ms_gemm_oz"] > 0:
+        out["ozaki_fp64_equivalent_tflops"] = st["flop_gemm_oz"] / (st["ms_gemm_oz"] / 1e3) / 1e12
+    return out
 
 
 def _sampled_rel_err(F, idx, w, precision, tt=None):
@@ -302,31 +353,67 @@ def _sampled_rel_err(F, idx, w, precision, tt=None):
     return err
 
 
-def _mixed(args, F, idx, vals, w, flush, stream):
-    """The same workload in mixed precision (split-TF32 tensor-core contractions)."""
-    import torch
-    for _ in range(args.warmup):
-        F.fasttt_decompose(idx, vals, w.dims, w.eps, precision="mixed").free()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    st = None
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
-        tt = F.fasttt_decompose(idx, vals, w.dims, w.eps, precision="mixed")
-        ev[i][1].record(stream)
-        st = tt.stats
-        if i < args.steps - 1:
-            tt.free()
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+def _mixed(args, F, idx, vals, w, flush, stream, fp64_ms):
+    """The headline workload in mixed precision: FP32-level tensor-core contractions
+    (3 exact bf16 slices) where a bond's rank decision is resolved at that level, FP64-level
+    products where it is not; FP64 Cholesky, rank decisions and error bookkeeping."""
+    steps = max(3, args.steps // 4)
+    tt, stats, ms_list = _time_steps(F, idx, vals, w, steps, min(args.warmup, 2), flush, stream, precision="mixed")
+    ms = sum(ms_list) / steps
     err = _sampled_rel_err(F, idx, w, "mixed", tt)
+    st = stats[-1]
     tt.free()
-    tc = st["ms_gemm_tc"]
-    return {"value": w.nnz / (ms / 1e3), "unit": "nnz/s", "ms_per_step": ms, "rel_err_sampled": err,
-            "ranks": st["ranks"], "dtype": "bf16-slice (3 slices) tensor-core contractions + f32/f64",
-            "tensor_gemm": {"ms": tc, "tflops": st["flop_gemm_tc"] / (tc / 1e3) / 1e12 if tc else None},
-            "stages_ms": {k: st[k] for k in ("ms_round", "ms_gemm_oz", "ms_gemm_tc", "ms_gemm", "ms_jacobi", "ms_tsqr",
-                                              "ms_tridiag32", "ms_tridiag", "ms_tdeig", "ms_jacobi32")}}
+    return {"value": w.nnz / (ms / 1e3), "unit": "nnz/s", "ms_per_step": ms, "steps": steps,
+            "speedup_vs_fp64": fp64_ms / ms, "rel_err_sampled": err, "meets_err_bar": err <= ERR_BAR,
+            "ranks": st["ranks"], "dtype": "bf16-slice (3 slices, FP32-level) tensor-core contractions + f64",
+            "stages_ms": {k: st[k] for k in STAGE_KEYS}, "routes": {k: st[k] for k in ROUTE_KEYS}}
+
+
+def _configs(args, F, dev, flush, stream, world):
+    """The other configurations, each in FP64 and in mixed precision: the 5-way 50^5 tensor
+    (1e5 nnz, eps 1e-8; 3 timed steps after 2 warm-ups), the Zipf 100^8 tensor (1e7 nnz,
+    FP32 values, eps 1e-4, rank cap 64) and the clustered 64^12 tensor (5e7 nnz, eps 1e-5,
+    rank cap 128), one timed call each (they take seconds to minutes)."""
+    import torch
+    from paper_1908_02721_gb300 import workloads as W
+    out = {}
+    plan = [("uniform5_50x5", lambda: W.uniform5(seed=2), 3, 2),
+            ("zipf8_100x8", lambda: W.zipf_tt(), 1, 0)]
+    if world == 1 and not args.no_config5:
+        plan.append(("clustered12_64x12", lambda: W.clustered(), 1, 0))
+    for name, make, steps, warm in plan:
+        entry = {}
+        try:
+            t = time.perf_counter()
+            w = make()
+            entry["workload"] = w.name
+            entry["generate_s"] = time.perf_counter() - t
+            entry["nnz"] = w.nnz
+            entry["eps"] = w.eps
+            entry["max_rank"] = w.max_rank
+            idx = torch.from_numpy(w.idx).to(dev)
+            vals = torch.from_numpy(w.vals).to(dev)
+            for prec in ("fp64", "mixed"):
+                try:
+                    tt, stats, ms_list = _time_steps(F, idx, vals, w, steps, warm, flush, stream, precision=prec)
+                    st = stats[-1]
+                    ms = sorted(ms_list)[len(ms_list) // 2]
+                    entry[prec] = {"ms": ms, "nnz_per_s": w.nnz / (ms / 1e3), "p": st["p"], "ranks": st["ranks"],
+                                   "rt_max": max(st["rt"]), "rel_err_sampled": _sampled_rel_err(F, idx, w, prec, tt),
+                                   "err_bound": math.sqrt(max(st["err2"], 0.0) / st["norm2"]),
+                                   "stages_ms": {k: st[k] for k in STAGE_KEYS},
+                                   "routes": {k: st[k] for k in ROUTE_KEYS}}
+                    tt.free()
+                except Exception as e:
+                    entry[prec] = {"error": str(e)[:300]}
+            if "ms" in entry.get("fp64", {}) and "ms" in entry.get("mixed", {}):
+                entry["mixed_speedup_vs_fp64"] = entry["fp64"]["ms"] / entry["mixed"]["ms"]
+            del idx, vals, w
+            torch.cuda.empty_cache()
+        except Exception as e:
+            entry["error"] = str(e)[:300]
+        out[name] = entry
+    return out
 
 
 def _adjoint(args, F, dev, stream):
@@ -398,9 +485,8 @@ def _next_rows(F, dev, stream):
     """One timed decomposition for each extension and further workload that runs through
     fasttt_decompose: dynamic truncation (Alg. 8) on the 50^5 workload; the FDM 7-point
     matrices of Table 2 (3-way MPO, p = 2, eps = 1e-14) at n = 20, 30, 40; the banded
-    2^20 x 2^20 matrix as a 20-way QTT through the exact grouping (S1-S5), and the
-    2^12 x 2^12 one through the whole pipeline in FP64 and mixed precision.  Each after one
-    warm-up call; failures are reported in the object."""
+    2^20 x 2^20 matrix as a 20-way QTT through the exact grouping (S1-S5, Alg. 9 over all
+    20 splits).  Each after one warm-up call; failures are reported in the object."""
     import torch
     from paper_1908_02721_gb300 import workloads as W
 
@@ -449,16 +535,6 @@ def _next_rows(F, dev, stream):
         tt.free()
     except Exception as e:
         qtt["m20_exact_grouping"] = {"error": str(e)[:300]}
-    for prec in ("fp64", "mixed"):   # the whole pipeline where its ranks stay dense-sized
-        try:
-            w = W.banded_qtt(12)
-            idx, vals = torch.from_numpy(w.idx).to(dev), torch.from_numpy(w.vals).to(dev)
-            tt, ms = timed(lambda: F.fasttt_decompose(idx, vals, w.dims, w.eps, precision=prec))
-            qtt[f"m12_{prec}"] = {"workload": w.name, "nnz": w.nnz, "ms": ms, "p": tt.stats["p"],
-                                  "rank_max": max(tt.ranks), "rel_err_sampled": _sampled_rel_err(F, idx, w, prec, tt)}
-            tt.free()
-        except Exception as e:
-            qtt[f"m12_{prec}"] = {"error": str(e)[:300]}
     out["banded_qtt"] = qtt
     return out
 
@@ -546,8 +622,10 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision pass")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-tt-round", action="store_true", help="skip the TT-rounding (Alg. 2) measurement")
-    ap.add_argument("--workload", default="uniform5", choices=["uniform5", "uniform5-n30"],
-                    help="uniform5-n30: the same recipe at 30^5, for profiler captures only")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations")
+    ap.add_argument("--no-config5", action="store_true", help="skip the 5e7-nonzero configuration")
+    ap.add_argument("--workload", default="qtt12", choices=["qtt12", "qtt10"],
+                    help="qtt10: the same recipe at 2^10 x 2^10, for profiler captures only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -29,6 +30,7 @@ namespace fasttt {
 namespace {
 
 constexpr int kLeaf = 64;
+constexpr int kMaxDevices = 64;
 
 #define CHOL_GRID_STRIDE(i, n)                                                     \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
@@ -56,10 +58,11 @@ __global__ void chol_leaf_kernel(double* H, int64_t ld, int nb, double tiny, int
     __syncthreads();   // every thread has read A[k][k]
     for (int j = k + threadIdx.x; j < nb; j += blockDim.x) A[k][j] = (j == k) ? rk : A[k][j] / rk;
     __syncthreads();
-    const int m = nb - k - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j >= i) A[i][j] -= A[k][i] * A[k][j];
+    // trailing update of the upper triangle: a warp per row, lanes along it
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = k + 1 + warp; i < nb; i += nw) {
+      const double aki = A[k][i];
+      for (int j = i + lane; j < nb; j += 32) A[i][j] -= aki * A[k][j];
     }
     __syncthreads();
   }
@@ -71,11 +74,16 @@ __global__ void chol_leaf_kernel(double* H, int64_t ld, int nb, double tiny, int
 
 // Forward substitution R^T X = B for the nb x nb upper R at R (leading dimension
 // ldr), B (nb rows x ncols, row stride ldb, unit column stride) overwritten by X.
-// One thread per column of B, the solution kept in registers.
+// One thread per column of B; the block's NB x 128 tile of B is staged in shared
+// memory with all its loads in flight at once, so the substitution chain reads
+// shared memory only, and the solution is kept in registers.
+constexpr int kTrsmCols = 128;
 template <int NB>
-__global__ void __launch_bounds__(128) trsm_leaf_kernel(const double* R, int64_t ldr, int nb, double* B, int64_t ldb,
-                                                        int64_t ncols) {
-  __shared__ double L[NB][NB + 1];   // L = R^T, identity-padded to NB
+__global__ void __launch_bounds__(kTrsmCols) trsm_leaf_kernel(const double* R, int64_t ldr, int nb, double* B,
+                                                              int64_t ldb, int64_t ncols) {
+  extern __shared__ double tsm[];
+  double(*L)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(tsm);            // L = R^T, identity-padded
+  double(*T)[kTrsmCols + 1] = reinterpret_cast<double(*)[kTrsmCols + 1]>(tsm + NB * (NB + 1));
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int i = e / NB, j = e % NB;
     double v;
@@ -83,13 +91,15 @@ __global__ void __launch_bounds__(128) trsm_leaf_kernel(const double* R, int64_t
     else v = (i == j) ? 1.0 : 0.0;
     L[i][j] = v;
   }
+  const int64_t c0 = (int64_t)blockIdx.x * kTrsmCols;
+  const int64_t c = c0 + threadIdx.x;
+  for (int i = 0; i < nb; ++i) T[i][threadIdx.x] = (c < ncols) ? B[(int64_t)i * ldb + c] : 0.0;
   __syncthreads();
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= ncols) return;
   double x[NB];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
-    double acc = (i < nb) ? B[(int64_t)i * ldb + c] : 0.0;
+    double acc = (i < nb) ? T[i][threadIdx.x] : 0.0;
 #pragma unroll
     for (int j = 0; j < i; ++j) acc -= L[i][j] * x[j];
     x[i] = acc / L[i][i];
@@ -234,7 +244,17 @@ void trsm_rt(const double* R, int64_t ldr, int64_t n, double* B, int64_t ldb, in
              cudaStream_t s) {
   if (n <= 0 || ncols <= 0) return;
   if (n <= kLeaf) {
-    trsm_leaf_kernel<kLeaf><<<(unsigned)ceil_div(ncols, 128), 128, 0, s>>>(R, ldr, (int)n, B, ldb, ncols);
+    const size_t smem = sizeof(double) * ((size_t)kLeaf * (kLeaf + 1) + (size_t)kLeaf * (kTrsmCols + 1));
+    // the dynamic shared-memory opt-in, once per device (setting it again is harmless)
+    static std::atomic<bool> attr[kMaxDevices];
+    int dev = 0;
+    FTT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices || !attr[dev].load()) {
+      FTT_CUDA(cudaFuncSetAttribute(trsm_leaf_kernel<kLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      if (dev >= 0 && dev < kMaxDevices) attr[dev].store(true);
+    }
+    trsm_leaf_kernel<kLeaf><<<(unsigned)ceil_div(ncols, kTrsmCols), kTrsmCols, smem, s>>>(R, ldr, (int)n, B, ldb,
+                                                                                          ncols);
     FTT_LAUNCH();
     return;
   }
@@ -313,12 +333,29 @@ bool cholqr2_rows(double* Z, int64_t M, int64_t N, double* R, bool mixed, cudaSt
   // level times its order
   const double u = mixed ? 0x1p-23 : 0x1p-52;
   const double tiny_rel = 4.0 * (double)M * u;
-  DBuf<double> H1((size_t)M * M, s), H2((size_t)M * M, s);
+  DBuf<double> H1((size_t)M * M, s);
   // pass 1: H1 = Z Z^T = R1^T R1, Z <- R1^-T Z
   gemm(mixed, M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, H1.get(), M, 1, s, true);
+  if (!R) {
+    // Z's rows already nearly orthonormal (a re-orthonormalisation): R1 is within 0.1 of
+    // I, so one pass leaves Q orthonormal to the Gram's rounding level, and R1^-T is
+    // applied as one GEMM (its condition number is below 1.2)
+    const double dev1 = identity_deviation(H1.get(), M, s);
+    if (dev1 <= 0.1) {
+      if (dev_out) *dev_out = dev1;
+      if (!cholesky_upper(H1.get(), M, tiny_rel, s)) return false;
+      DBuf<double> X((size_t)M * M, s), Z0((size_t)M * N, s);
+      identity_f64(X.get(), M, s);
+      trsm_upper_t(H1.get(), M, X.get(), M, M, false, s);   // X = R1^-T
+      FTT_CUDA(cudaMemcpyAsync(Z0.get(), Z, sizeof(double) * M * N, cudaMemcpyDeviceToDevice, s));
+      gemm(mixed, M, N, M, 1.0, X.get(), M, 1, Z0.get(), N, 1, 0.0, Z, N, 1, s);
+      return true;
+    }
+  }
   if (!cholesky_upper(H1.get(), M, tiny_rel, s)) return false;
   trsm_upper_t(H1.get(), M, Z, N, N, mixed, s);
   // pass 2 on a matrix that is now well conditioned
+  DBuf<double> H2((size_t)M * M, s);
   gemm(mixed, M, M, N, 1.0, Z, N, 1, Z, 1, N, 0.0, H2.get(), M, 1, s, true);
   const double dev = identity_deviation(H2.get(), M, s);
   if (dev_out) *dev_out = dev;

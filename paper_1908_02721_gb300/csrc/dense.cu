@@ -1203,6 +1203,7 @@ struct EigStart {
   DBuf<double> V;
   std::vector<double> lam;
   bool ok = false;
+  bool declined = false;   // the start did not apply: the retry goes to the FP64 routes
 };
 
 // Eigenpairs of the symmetric Gram G (n x n) into V (row j = eigenvector j) and h.
@@ -1210,15 +1211,22 @@ struct EigStart {
 // level: the stored start refined with FP64-level products if there is one, else
 // the fast route, then the FP64 tridiagonal route, then the iterative one.
 bool gram_eig(const double* G, int n, double* V, std::vector<double>& h, int64_t max_sweeps, cudaStream_t s,
-              bool mixed, EigStart& st0, int64_t& sweeps) {
+              bool mixed, EigStart& st0, int64_t& sweeps,
+              const std::function<bool(const std::vector<double>&)>& start_ok = nullptr) {
   sweeps = 0;
   const int64_t nn = (int64_t)n * n;
   if (mixed) {
-    if (!sym_eig_start_f32(G, n, V, h, s)) return false;
+    if (!sym_eig_start_f32(G, n, V, h, s)) {
+      st0.declined = true;
+      return false;
+    }
     st0.V = DBuf<double>(nn, s);
     FTT_CUDA(cudaMemcpyAsync(st0.V.get(), V, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
     st0.lam = h;
     st0.ok = true;
+    // a bond that the start already shows to be unresolvable at FP32 level goes to
+    // FP64 before any FP32-level refinement is spent on it
+    if (start_ok && !start_ok(h)) return false;
     if (!refine_eig(G, n, V, h, max_sweeps, s, true)) return false;
     note_eig_fast();
     return true;
@@ -1230,7 +1238,7 @@ bool gram_eig(const double* G, int n, double* V, std::vector<double>& h, int64_t
       note_eig_fast();
       return true;
     }
-  } else if (sym_eig_fast(G, n, V, h, max_sweeps, s, false)) {
+  } else if (!st0.declined && sym_eig_fast(G, n, V, h, max_sweeps, s, false)) {
     return true;
   }
   const bool td = sym_eig_tridiag(G, n, V, h, s, false);
@@ -1246,8 +1254,29 @@ int64_t mixed_bonds_escalated() { return g_mixed_escalated.load(); }
 
 namespace {
 
-// Direct route: one-sided Jacobi (through TSQR for tall-skinny shapes) on the
-// tall orientation of Z, FP64 whatever the precision.
+// Tall-skinny shapes wider than TSQR takes (lg >= 4n, n > kMaxTsqrCols): the tall
+// orientation T (A, column-major lg x n) = Q R by FP64 CholeskyQR2, one-sided Jacobi
+// on the n x n R only (R V = U_R Sigma), then A <- Q (R V) = T V by one FP64-level
+// GEMM: the same result as Jacobi on T (backward error u ||T||) with the sweeps on n
+// rows instead of lg.  False, A untouched, when the shape does not apply or
+// CholeskyQR2 breaks down (T too ill conditioned): the caller runs Jacobi on T.
+bool cholqr_jacobi(double* A, int64_t lg, int n, double* V, int64_t max_sweeps, cudaStream_t s, int64_t& sweeps) {
+  if (n <= kMaxTsqrCols || lg < 4 * (int64_t)n) return false;
+  const int64_t nn = (int64_t)n * n;
+  DBuf<double> Q((size_t)lg * n, s), R(nn, s), Rc(nn, s);
+  FTT_CUDA(cudaMemcpyAsync(Q.get(), A, sizeof(double) * lg * n, cudaMemcpyDeviceToDevice, s));
+  // A's memory is row-major n x lg (rows = columns of T): CholeskyQR2 of its rows gives
+  // A = R^T Q, i.e. T = Q^T R with Q^T's columns orthonormal
+  if (!cholqr2_rows(Q.get(), n, lg, R.get(), false, s)) return false;
+  transpose_f64(R.get(), n, n, Rc.get(), s);   // column-major R
+  sweeps = jacobi_f64(Rc.get(), n, n, n, V, n, n, max_sweeps, s);
+  // A (column-major lg x n) = Q^T (lg x n) . Rc:  A(i, j) = sum_k Q[k lg + i] Rc[j n + k]
+  gemm_f64(lg, n, n, 1.0, Q.get(), 1, lg, Rc.get(), 1, n, 0.0, A, 1, lg, s);
+  return true;
+}
+
+// Direct route: one-sided Jacobi (through TSQR or CholeskyQR2 for tall-skinny
+// shapes) on the tall orientation of Z, FP64 whatever the precision.
 void svd_direct(const double* Z, int64_t M, int64_t N,
                 const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
                 SvdOut& out, cudaStream_t s) {
@@ -1261,8 +1290,11 @@ void svd_direct(const double* Z, int64_t M, int64_t N,
   std::vector<double> h(n);
   identity_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(V.get(), n);
   FTT_LAUNCH();
-  if (tsqr_applies(lg, n)) out.sweeps = tsqr_jacobi(A.get(), lg, n, V.get(), max_sweeps, s);
-  else out.sweeps = jacobi_f64(A.get(), lg, lg, n, V.get(), n, n, max_sweeps, s);
+  if (tsqr_applies(lg, n)) {
+    out.sweeps = tsqr_jacobi(A.get(), lg, n, V.get(), max_sweeps, s);
+  } else if (!cholqr_jacobi(A.get(), lg, n, V.get(), max_sweeps, s, out.sweeps)) {
+    out.sweeps = jacobi_f64(A.get(), lg, lg, n, V.get(), n, n, max_sweeps, s);
+  }
   {
     DBuf<double> norms(n, s);
     col_norms_kernel<double><<<n, 256, 0, s>>>(A.get(), lg, lg, n, norms.get());
@@ -1325,16 +1357,26 @@ bool svd_gram(const double* Z, int64_t M, int64_t N,
   DBuf<double> V((size_t)n * n, s);
   std::vector<double> h(n);
   int64_t sweeps = 0;
-  if (!gram_eig(A.get(), n, V.get(), h, max_sweeps, s, mixed, st0, sweeps)) return false;
+  // mixed: the error floor of the FP32-level route = the probed distance of the Gram from
+  // Z^T Z (Z Z^T) plus the rounding level of the FP32-level eigen-refinement; the FP32
+  // start is tested against it with its own error (FP32 tridiagonalisation) added
+  const double gram_err = mixed ? 4.0 * gram_error_probe(Z, M, N, A.get(), s) : 0.0;
+  auto floor_of = [&](const std::vector<double>& lam, double c) {
+    double lmax = 0.0;
+    for (double x : lam) lmax = std::max(lmax, fabs(x));
+    return gram_err + c * sqrt((double)n) * lmax;
+  };
+  auto start_ok = [&](const std::vector<double>& lam) {
+    std::vector<double> sg;
+    std::vector<int32_t> pm;
+    sigma_from_lambda(lam, sg, pm);
+    return rank_is_resolved(choose_rank, sg, n, floor_of(lam, 0x1p-21));
+  };
+  if (!gram_eig(A.get(), n, V.get(), h, max_sweeps, s, mixed, st0, sweeps, start_ok)) return false;
   out.sweeps = sweeps;
   std::vector<int32_t> perm;
   sigma_from_lambda(h, out.sigma_all, perm);
-  if (mixed) {
-    double lmax = 0.0;
-    for (double x : h) lmax = std::max(lmax, fabs(x));
-    const double floor = 4.0 * gram_error_probe(Z, M, N, A.get(), s) + 0x1p-21 * sqrt((double)n) * lmax;
-    if (!rank_is_resolved(choose_rank, out.sigma_all, n, floor)) return false;
-  }
+  if (mixed && !rank_is_resolved(choose_rank, out.sigma_all, n, floor_of(h, 0x1p-23))) return false;
   A.reset();
   int64_t r = choose_rank(out.sigma_all);
   r = std::max<int64_t>(1, std::min<int64_t>(r, n));
@@ -1445,12 +1487,21 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
   if (mixed) {
     // The Gram is an FP64 sum here: the error floor is the FP32-level refinement's
     int64_t sw = 0;
-    if (gram_eig(Gram, n, V.get(), h, max_sweeps, s, true, st0, sw)) {
+    auto start_ok = [&](const std::vector<double>& lam) {
+      std::vector<double> sg;
+      std::vector<int32_t> pm;
+      sigma_from_lambda(lam, sg, pm);
+      double lmax = 0.0;
+      for (double x : lam) lmax = std::max(lmax, fabs(x));
+      sg.resize(nsv);
+      return rank_is_resolved(choose_rank, sg, nsv, 0x1p-21 * sqrt((double)n) * lmax);
+    };
+    if (gram_eig(Gram, n, V.get(), h, max_sweeps, s, true, st0, sw, start_ok)) {
       sigma_from_lambda(h, out.sigma_all, perm);
       double lmax = 0.0;
       for (double x : h) lmax = std::max(lmax, fabs(x));
       out.sigma_all.resize(nsv);
-      done = rank_is_resolved(choose_rank, out.sigma_all, nsv, 0x1p-21 * sqrt((double)n) * lmax);
+      done = rank_is_resolved(choose_rank, out.sigma_all, nsv, 0x1p-23 * sqrt((double)n) * lmax);
       out.sweeps = sw;
     }
     (done ? g_mixed_kept : g_mixed_escalated).fetch_add(1);

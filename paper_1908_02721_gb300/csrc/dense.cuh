@@ -159,7 +159,9 @@ double identity_deviation(const double* H, int64_t n, cudaStream_t s);
 // Grams and the solve updates are FP32-level products when mixed; the Cholesky
 // factorisations and R = R2 R1 are FP64.  False (Z undefined) on a Cholesky
 // breakdown or when the second Gram is further than 0.5 from I (Z too ill
-// conditioned for the Gram's precision); dev_out gets that distance.
+// conditioned for the Gram's precision); dev_out gets that distance.  Without R
+// (a re-orthonormalisation) and with ||Z Z^T - I||_F <= 0.1, one pass suffices:
+// Z <- R1^-T Z as one GEMM.
 bool cholqr2_rows(double* Z, int64_t M, int64_t N, double* R, bool mixed, cudaStream_t s, double* dev_out = nullptr);
 
 // The columns of the row-major rows x r matrix U made orthonormal by CholeskyQR2
