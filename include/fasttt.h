@@ -146,6 +146,7 @@ typedef struct fasttt_stats {
   int64_t qr_svd;             /* QR steps that fell back to an untruncated SVD (CholeskyQR2 broke down) */
   int64_t mixed_fp32_bonds;   /* mixed precision: Gram-route SVDs whose FP32-level result was kept */
   int64_t mixed_fp64_bonds;   /* mixed precision: Gram-route SVDs redone with FP64-level products */
+  int64_t wait_timeouts;      /* device spin-waits of this call that gave up (see max_spin) */
 } fasttt_stats;
 
 typedef struct fasttt_tt fasttt_tt; /* opaque result handle */
@@ -286,22 +287,24 @@ int tt_eval_backward(int d, const int64_t* dims, const int64_t* ranks,
 
 /*
  * tt_eval_backward_noalloc — for callers that cannot call cudaMalloc (or any
- * allocator) on the device: for example code running inside a stream capture
- * that must not allocate, a host framework that owns all device memory through
- * its own pool, or an embedded runtime with a fixed memory budget.  The paper
- * has no counterpart; this is a library-level service.
+ * allocator) on the device: for example a host framework that owns all device
+ * memory through its own pool, or an embedded runtime with a fixed memory budget.
+ * The paper has no counterpart; this is a library-level service.
  * Same arguments and result as tt_eval_backward with recompute = 0 (gradients
- * ADDED into d_grad_cores).  Its scratch is a file-scope device array of
+ * ADDED into d_grad_cores, which the caller allocates at the cores' shapes and
+ * dtype).  Its scratch is a file-scope device array of
  * FASTTT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
- * the process exits; the call allocates nothing.  The first call on a device
- * looks up that array's device address (with the device current); make that
- * first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (other streams, other threads) race: serialise
- * them.  The scratch holds, per resident warp, the left partial products
- * (r_0 + ... + r_{d-1} values); one thread block of up to 8 warps must fit, so
- * calls whose r_0 + ... + r_{d-1} exceeds 524,000 (FP64) or 1,048,000 (FP32) are
- * rejected with FASTTT_ERANK and a message saying so; smaller sums only limit
- * how many warps run at once.  Other errors as tt_eval_backward.
+ * the process exits; the call allocates nothing.  Every call looks up that
+ * array's device address with the caller's device current.  The call reads the
+ * kernel's error flag back, so it synchronises the stream before returning.  All
+ * calls share the one array, so calls that overlap on the GPU (other streams,
+ * other threads) race: serialise them.  The scratch holds, per resident warp, the
+ * left partial products (r_0 + ... + r_{d-1} values of the cores' dtype) after a
+ * 256-byte error word; the grid is limited to the warps that fit, and a call is
+ * rejected with FASTTT_ERANK only when not even one thread block's warps fit.
+ * Within this library's limits (d <= 64, ranks <= 8192, so
+ * r_0 + ... + r_{d-1} <= 516,097) one block always fits, so large rank sums only
+ * lower the number of warps at work.  Other errors as tt_eval_backward.
  */
 #define FASTTT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int tt_eval_backward_noalloc(int d, const int64_t* dims, const int64_t* ranks,

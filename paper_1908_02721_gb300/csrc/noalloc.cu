@@ -4,8 +4,6 @@
 // that loads this library holds until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "common.cuh"
 
 namespace fasttt {
@@ -21,23 +19,13 @@ constexpr size_t kScratchBytes = FASTTT_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Host code cannot use g_noalloc_scratch's name as a device address: it is a
-// host-side stand-in.  The device address is looked up once per device, with
-// that device current, and cached here.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
+// host-side stand-in.  The device address is looked up on every call, with the
+// caller's device current (the lookup allocates nothing), so it always names the
+// array of the context the call runs in, also after a device reset.
 void* scratch_for_current_device() {
-  int dev = -1;
-  FTT_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) ::fasttt::fail(FASTTT_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* ptr = nullptr;
-    FTT_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_addr[dev] = ptr;
-  }
-  return g_addr[dev];
+  void* ptr = nullptr;
+  FTT_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+  return ptr;
 }
 
 }  // namespace

@@ -69,7 +69,7 @@ class Stats(ctypes.Structure):
                 ("ms_tridiag32", ctypes.c_double), ("flop_tridiag32", ctypes.c_double),
                 ("ms_tsqr", ctypes.c_double), ("flop_tsqr", ctypes.c_double), ("eig_fast", ctypes.c_int64),
                 ("qr_cholqr2", ctypes.c_int64), ("qr_svd", ctypes.c_int64), ("mixed_fp32_bonds", ctypes.c_int64),
-                ("mixed_fp64_bonds", ctypes.c_int64)]
+                ("mixed_fp64_bonds", ctypes.c_int64), ("wait_timeouts", ctypes.c_int64)]
 
     def to_dict(self):
         d = self.d
@@ -92,7 +92,8 @@ class Stats(ctypes.Structure):
                 "flop_gemm_oz": self.flop_gemm_oz, "ms_tridiag32": self.ms_tridiag32,
                 "flop_tridiag32": self.flop_tridiag32, "ms_tsqr": self.ms_tsqr, "flop_tsqr": self.flop_tsqr,
                 "eig_fast": self.eig_fast, "qr_cholqr2": self.qr_cholqr2, "qr_svd": self.qr_svd,
-                "mixed_fp32_bonds": self.mixed_fp32_bonds, "mixed_fp64_bonds": self.mixed_fp64_bonds}
+                "mixed_fp32_bonds": self.mixed_fp32_bonds, "mixed_fp64_bonds": self.mixed_fp64_bonds,
+                "wait_timeouts": self.wait_timeouts}
 
 
 _P = ctypes.c_void_p
@@ -149,11 +150,14 @@ class FastTTError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"[{code}] {msg}")
         self.code = code
+        self.stats = None
 
 
-def _check(rc):
+def _check(rc, stats=None):
     if rc != OK:
-        raise FastTTError(rc, _lib.fasttt_last_error().decode())
+        err = FastTTError(rc, _lib.fasttt_last_error().decode())
+        err.stats = stats.to_dict() if stats is not None else None
+        raise err
 
 
 def version() -> str:
@@ -338,12 +342,14 @@ class TT:
 
 def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True, rounding="static",
                      stage="full", keep_intermediates=False, max_sweeps=0, precision="fp64", sparse_sweep="auto",
-                     gemm_engine="tensor", stream=None) -> TT:
+                     gemm_engine="tensor", max_spin=0, stream=None) -> TT:
     """FastTT (Alg. 7) of the COO tensor (idx (d, nnz) int32, vals float64/float32).
 
     sparse_sweep: "auto", "sparse" or "dense", how the first SVD sweep holds its cores.
     gemm_engine: "tensor" (large FP64 products on the tensor cores from exact bf16 slices)
-    or "dfma" (FP64 DFMA only)."""
+    or "dfma" (FP64 DFMA only).  max_spin > 0 bounds every device spin-wait at that many
+    polls; a wait that gives up fails the call with ETIMEOUT.  On failure the raised
+    FastTTError carries the call's statistics in .stats."""
     _require_cuda()
     idx = _dev(idx, torch.int32)
     if isinstance(vals, np.ndarray):
@@ -369,12 +375,13 @@ def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True
     if gemm_engine not in GEMM_ENGINES:
         raise FastTTError(EINVAL, "gemm_engine must be 'tensor' or 'dfma'")
     o.gemm_engine = GEMM_ENGINES[gemm_engine]
+    o.max_spin = int(max_spin)
     out = ctypes.c_void_p(0)
     st = Stats()
     rc = _lib.fasttt_decompose(d, _i64arr(dims), int(idx.shape[1]), ctypes.c_void_p(idx.data_ptr()),
                                ctypes.c_void_p(vals.data_ptr()), vdtype, float(eps), ctypes.byref(o),
                                _stream(stream), ctypes.byref(out), ctypes.byref(st))
-    _check(rc)
+    _check(rc, st)
     return TT(out.value, dims)
 
 
@@ -401,7 +408,7 @@ def _fp64_tt(x):
 
 
 def tt_round(tt, eps, *, max_rank=0, precision="fp64", max_sweeps=0, gemm_engine="tensor",
-             keep_intermediates=False, stream=None) -> TT:
+             keep_intermediates=False, max_spin=0, stream=None) -> TT:
     """TT-rounding (Alg. 2) of a TT given as a handle or as FP64 CUDA cores, to relative
     accuracy eps (eps = 0: numerical ranks); max_rank caps every rank.  Returns a new handle."""
     _require_cuda()
@@ -417,6 +424,7 @@ def tt_round(tt, eps, *, max_rank=0, precision="fp64", max_sweeps=0, gemm_engine
     if gemm_engine not in GEMM_ENGINES:
         raise FastTTError(EINVAL, "gemm_engine must be 'tensor' or 'dfma'")
     o.gemm_engine = GEMM_ENGINES[gemm_engine]
+    o.max_spin = int(max_spin)
     out = ctypes.c_void_p(0)
     st = Stats()
     rc = _lib.fasttt_tt_round(d, _i64arr(dims), _i64arr(ranks), ptrs, float(eps), ctypes.byref(o), _stream(stream),
@@ -441,14 +449,57 @@ def tt_add(a, b, beta=1.0, stream=None) -> TT:
     return TT(out.value, dims)
 
 
-def _core_args(cores):
-    d = len(cores)
-    dtype = cores[0].dtype
+def _check_cores(cores):
+    """Shapes and dtypes of a TT's cores, before any device is needed: d >= 1 contiguous
+    (r_{k-1}, n_k, r_k) tensors of one dtype (float64 or float32), r_0 = r_d = 1 and
+    adjacent ranks equal.  Returns d."""
+    if not isinstance(cores, (list, tuple)) or len(cores) < 1 or len(cores) > MAX_D:
+        raise FastTTError(EINVAL, "cores must be a list of 1..64 tensors")
+    dtype = getattr(cores[0], "dtype", None)
     if dtype not in (torch.float64, torch.float32):
         raise FastTTError(EINVAL, "cores must be float64 or float32")
     for G in cores:
-        if G.dtype != dtype or G.device.type != "cuda" or not G.is_contiguous() or G.dim() != 3:
-            raise FastTTError(EINVAL, "cores must be contiguous CUDA tensors (r0, n, r1) of one dtype")
+        if not isinstance(G, torch.Tensor) or G.dtype != dtype or G.dim() != 3 or not G.is_contiguous():
+            raise FastTTError(EINVAL, "cores must be contiguous tensors (r0, n, r1) of one dtype")
+    if cores[0].shape[0] != 1 or cores[-1].shape[2] != 1:
+        raise FastTTError(EINVAL, "r_0 and r_d must be 1")
+    for a, b in zip(cores[:-1], cores[1:]):
+        if a.shape[2] != b.shape[0]:
+            raise FastTTError(EINVAL, "adjacent cores disagree on their rank")
+    return len(cores)
+
+
+def _check_entries(d, idx, grad_out=None):
+    """idx (d, m) and, for the adjoint, grad_out (m,), before any device is needed."""
+    shape = tuple(getattr(idx, "shape", np.shape(idx)))
+    if len(shape) != 2 or shape[0] != d:
+        raise FastTTError(EINVAL, "idx must have shape (d, m)")
+    if grad_out is not None:
+        gshape = tuple(getattr(grad_out, "shape", np.shape(grad_out)))
+        if gshape != (shape[1],):
+            raise FastTTError(EINVAL, "grad_out must have shape (m,)")
+    return shape[1]
+
+
+def _check_grad_cores(cores, grad_cores):
+    """Caller-provided gradient cores: one per core, each of its core's shape, dtype and
+    device, contiguous (the kernels add into them at the core's layout)."""
+    if not isinstance(grad_cores, (list, tuple)) or len(grad_cores) != len(cores):
+        raise FastTTError(EINVAL, "grad_cores must hold one tensor per core")
+    for g, G in zip(grad_cores, cores):
+        if (not isinstance(g, torch.Tensor) or g.shape != G.shape or g.dtype != G.dtype or g.device != G.device
+                or not g.is_contiguous()):
+            raise FastTTError(EINVAL, "every gradient core must be a contiguous tensor of its core's shape, dtype "
+                                      "and device")
+
+
+def _core_args(cores):
+    _check_cores(cores)
+    d = len(cores)
+    dtype = cores[0].dtype
+    for G in cores:
+        if G.device.type != "cuda":
+            raise FastTTError(EINVAL, "cores must be CUDA tensors")
     dims = [int(G.shape[1]) for G in cores]
     ranks = [int(cores[0].shape[0])] + [int(G.shape[2]) for G in cores]
     ptrs = (ctypes.c_void_p * d)(*[G.data_ptr() for G in cores])
@@ -475,6 +526,7 @@ def tt_fit_gd(cores, idx, vals, steps, lr, stream=None):
 
 def tt_eval_at(cores, idx, stream=None) -> torch.Tensor:
     """a(i^e) = G_1[i_1] ... G_d[i_d] for every column of idx (d, m)."""
+    _check_entries(_check_cores(cores), idx)
     _require_cuda()
     d, dims, ranks, ptrs, code, dtype = _core_args(cores)
     idx = _dev(idx, torch.int32)
@@ -487,6 +539,9 @@ def tt_eval_at(cores, idx, stream=None) -> torch.Tensor:
 
 def tt_eval_backward(cores, idx, grad_out, grad_cores=None, recompute=False, stream=None):
     """Adds dL/dG_k for L = sum_e grad_out[e] a(i^e) into grad_cores (zeros if None); returns them."""
+    _check_entries(_check_cores(cores), idx, grad_out)
+    if grad_cores is not None:
+        _check_grad_cores(cores, grad_cores)
     _require_cuda()
     d, dims, ranks, ptrs, code, dtype = _core_args(cores)
     idx = _dev(idx, torch.int32)
@@ -501,11 +556,15 @@ def tt_eval_backward(cores, idx, grad_out, grad_cores=None, recompute=False, str
 
 
 def tt_eval_backward_noalloc(cores, idx, grad_out, grad_cores, stream=None):
-    """tt_eval_backward for callers that cannot allocate device memory: the
-    library works in its fixed, process-lifetime scratch array instead.  The
-    caller provides every input and the (pre-allocated) gradient cores, which
-    receive the gradient ADDED to their contents.  Calls sharing the scratch
-    must not overlap on the GPU."""
+    """tt_eval_backward for callers that cannot allocate device memory (a framework
+    that owns all device memory through its own pool, a runtime with a fixed memory
+    budget): the library works in its fixed, process-lifetime scratch array instead.
+    The caller provides every input and the (pre-allocated) gradient cores, which
+    receive the gradient ADDED to their contents.  Every argument is checked here
+    before the call, since the kernels read and add at the shapes given.  Calls
+    sharing the scratch must not overlap on the GPU."""
+    _check_entries(_check_cores(cores), idx, grad_out)
+    _check_grad_cores(cores, grad_cores)
     _require_cuda()
     d, dims, ranks, ptrs, code, dtype = _core_args(cores)
     if idx.device.type != "cuda" or idx.dtype != torch.int32 or not idx.is_contiguous():

@@ -74,7 +74,7 @@ def test_struct_layouts_match_header(lib):
     assert F.Opts.sparse_sweep.offset == 6 * 4 + 2 * 8
     assert F.Opts.max_spin.offset == 8 * 4 + 2 * 8
     assert F.Stats.flop_gemm_oz.offset + 8 == F.Stats.ms_tridiag32.offset
-    assert F.Stats.mixed_fp64_bonds.offset + 8 == ctypes.sizeof(F.Stats)
+    assert F.Stats.wait_timeouts.offset + 8 == ctypes.sizeof(F.Stats)
 
 
 def test_calls_without_gpu_fail_loudly(lib):
@@ -110,3 +110,37 @@ def test_tt_arithmetic_and_fitting_fail_loudly_without_gpu(lib):
     losses = (ctypes.c_double * 2)()
     assert lib.tt_fit_gd(0, dims, bad_ranks, ptrs, 0, ctypes.c_int64(0), None, None, ctypes.c_int64(1),
                          ctypes.c_double(0.1), losses, None) == F.EINVAL
+
+
+def test_eval_and_adjoint_arguments_rejected_before_any_launch(lib):
+    """tt_eval_at, tt_eval_backward and tt_eval_backward_noalloc check the shapes the
+    kernels index with (idx (d, m), grad_out (m,), one gradient core per core of its
+    core's shape, dtype and device) before the call: a wrong shape is EINVAL, never an
+    out-of-bounds device access.  The checks need no GPU."""
+    import torch
+    from paper_1908_02721_gb300 import fasttt as F
+    cores = [torch.zeros((1, 3, 2), dtype=torch.float64), torch.zeros((2, 4, 1), dtype=torch.float64)]
+    idx = torch.zeros((2, 5), dtype=torch.int32)
+    g = torch.zeros(5, dtype=torch.float64)
+    grads = [torch.zeros_like(c) for c in cores]
+    bad = [
+        lambda: F.tt_eval_at(cores, torch.zeros((3, 5), dtype=torch.int32)),           # idx rows != d
+        lambda: F.tt_eval_at(cores, torch.zeros(5, dtype=torch.int32)),                # idx not 2-D
+        lambda: F.tt_eval_at([cores[0], torch.zeros((3, 4, 1), dtype=torch.float64)], idx),  # ranks disagree
+        lambda: F.tt_eval_backward(cores, idx, torch.zeros(4, dtype=torch.float64)),   # grad_out length
+        lambda: F.tt_eval_backward(cores, idx, g, [grads[0]]),                         # one gradient short
+        lambda: F.tt_eval_backward_noalloc(cores, idx, g, [grads[0], torch.zeros((2, 4, 2), dtype=torch.float64)]),
+        lambda: F.tt_eval_backward_noalloc(cores, idx, g, [grads[0], grads[1].float()]),   # dtype
+        lambda: F.tt_eval_backward_noalloc(cores, idx, torch.zeros((5, 1), dtype=torch.float64), grads),
+        lambda: F.tt_eval_backward_noalloc(cores, torch.zeros((1, 5), dtype=torch.int32), g, grads),
+    ]
+    for call in bad:
+        with pytest.raises(F.FastTTError) as e:
+            call()
+        assert e.value.code == F.EINVAL, str(e.value)
+    if not torch.cuda.is_available():   # well-formed arguments get as far as the missing device
+        for call in (lambda: F.tt_eval_at(cores, idx), lambda: F.tt_eval_backward(cores, idx, g),
+                     lambda: F.tt_eval_backward_noalloc(cores, idx, g, grads)):
+            with pytest.raises(F.FastTTError) as e:
+                call()
+            assert e.value.code == F.ECUDA

@@ -1,7 +1,11 @@
 """tt_eval_backward_noalloc: the adjoint for callers that cannot allocate device
-memory (the library uses its fixed scratch array instead).  Its result must
-match tt_eval_backward's, on two calls in a row (the scratch keeps the previous
-call's contents, which must not leak into the next result).
+memory, such as a framework that owns all device memory through its own pool or
+a runtime with a fixed memory budget.  The library works in its fixed scratch
+array instead.  Its gradients must match the FP64 oracle's closed form
+(oracle.tteval.tt_eval_grad) and the allocating entry point's, on two calls in a
+row: the scratch keeps the previous call's contents, which must not leak into
+the next result.  One case has rank sums large enough that the scratch, not the
+work, caps the number of warps (the grid sizing by what fits).
 
 Kept in its own file, named to be collected last.
 """
@@ -10,6 +14,8 @@ import math
 import numpy as np
 import pytest
 import torch
+
+from oracle import tteval as OT
 
 pytestmark = pytest.mark.gpu
 
@@ -20,23 +26,45 @@ def _tt(dims, ranks, seed, dtype):
                              .astype(dtype)).cuda() for k in range(len(dims))]
 
 
+def _check(F, cores, idx, g, tol):
+    out = [torch.zeros_like(c) for c in cores]
+    F.tt_eval_backward_noalloc(cores, idx, g, out)
+    ref_lib = F.tt_eval_backward(cores, idx, g, recompute=False)
+    torch.cuda.synchronize()
+    ref = OT.tt_eval_grad([c.cpu().numpy().astype(np.float64) for c in cores], idx.cpu().numpy(),
+                          g.cpu().numpy().astype(np.float64))
+    for a, b, r in zip(out, ref_lib, ref):
+        scale = max(1.0, float(np.abs(r).max()))
+        assert float(np.abs(a.cpu().numpy().astype(np.float64) - r).max()) <= tol * scale
+        assert (a - b).abs().max().item() <= tol * scale
+
+
 @pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 1e-5)])
-def test_noalloc_backward_matches_allocating_entry_point(dtype, tol):
+def test_noalloc_backward_matches_oracle(dtype, tol):
     from paper_1908_02721_gb300 import fasttt as F
     dims = [7, 9, 5, 6]
     rng = np.random.Generator(np.random.Philox(key=503))
     for call, ranks in enumerate([[1, 6, 12, 4, 1], [1, 30, 17, 45, 1]]):   # two calls in a row
         cores = _tt(dims, ranks, 501 + call, dtype)
-        m = 5000
+        m = 2000
         idx = torch.from_numpy(np.stack([rng.integers(0, n, m) for n in dims]).astype(np.int32)).cuda()
         g = torch.from_numpy(rng.standard_normal(m).astype(dtype)).cuda()
-        ref = F.tt_eval_backward(cores, idx, g, recompute=False)
-        out = [torch.zeros_like(c) for c in cores]
-        F.tt_eval_backward_noalloc(cores, idx, g, out)
-        torch.cuda.synchronize()
-        for a, b in zip(out, ref):
-            scale = max(1.0, b.abs().max().item())
-            assert (a - b).abs().max().item() <= tol * scale
+        _check(F, cores, idx, g, tol)
+
+
+def test_noalloc_grid_capped_by_scratch():
+    """64 modes of size 2 at ranks 16: a warp's left partials take (1 + 63 x 16) x 8 B,
+    so about 4,150 warps fit in the 32 MiB scratch, fewer than 6,000 entries would use."""
+    from paper_1908_02721_gb300 import fasttt as F
+    d, r = 64, 16
+    dims = [2] * d
+    ranks = [1] + [r] * (d - 1) + [1]
+    cores = _tt(dims, ranks, 701, np.float64)
+    rng = np.random.Generator(np.random.Philox(key=702))
+    m = 6000
+    idx = torch.from_numpy(np.stack([rng.integers(0, 2, m) for _ in dims]).astype(np.int32)).cuda()
+    g = torch.from_numpy(rng.standard_normal(m)).cuda()
+    _check(F, cores, idx, g, 1e-12)
 
 
 def test_noalloc_reports_bad_index():
