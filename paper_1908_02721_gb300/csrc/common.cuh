@@ -45,6 +45,20 @@ void note_eig_fast();
 // GEMM engine for the FP64 GEMMs of the calling thread: 0 = tensor cores (exact bf16
 // slices) for large products, 1 = FP64 DFMA only.
 void set_gemm_engine(int engine);
+// Poll bound of the device spin-waits for the calling thread's next calls (the
+// max_spin option): 0 = each wait's default bound, with the cooperative kernels
+// falling back to one launch per round when a grid barrier gives up; > 0 = that
+// bound, and a wait that gives up fails the call with FASTTT_ETIMEOUT.
+void set_max_spin(int64_t spins);
+int64_t max_spin();
+// Device waits that gave up since the library was loaded (statistics).
+void note_wait_timeout();
+int64_t wait_timeouts();
+// The grid-barrier poll bound to store in bar[3] (0 = the kernel's default).
+inline unsigned barrier_spins() {
+  const int64_t v = max_spin();
+  return v <= 0 ? 0u : (v > 0xFFFFFFFFll ? 0xFFFFFFFFu : (unsigned)v);
+}
 int gemm_engine();   // Gram eigensolver: tridiagonal route taken, or the iterative fallback
 
 #define FTT_CUDA(call) ::fasttt::cuda_check((call), #call, __FILE__, __LINE__)

@@ -589,7 +589,18 @@ int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ld
     for (T x : h) f2 += (double)x * (double)x;
     small2 = (T)(f2 * (f64 ? 0x1p-100 : 0x1p-42));  // (2^-50 or 2^-21 of ||A||_F)^2
   }
-  DBuf<unsigned> rot(4, s);  // [0] rotations, [1..3] grid barrier
+  DBuf<unsigned> rot(5, s);  // [0] rotations, [1..4] grid barrier (count, generation, error, poll bound)
+  auto reset_rot = [&]() {
+    FTT_CUDA(cudaMemsetAsync(rot.get(), 0, sizeof(unsigned), s));
+    barrier_init_kernel<<<1, 1, 0, s>>>(rot.get() + 1, barrier_spins());
+    FTT_LAUNCH();
+  };
+  // a grid barrier that gave up: with an explicit poll bound the call fails, otherwise
+  // the sweep is redone one launch per round
+  auto barrier_gave_up = [&]() {
+    note_wait_timeout();
+    if (max_spin() > 0) fail(FASTTT_ETIMEOUT, "a grid barrier of the Jacobi sweep exceeded max_spin polls");
+  };
   const double pairs = 0.5 * (double)n * (double)(n - 1);
   // cooperative grid: every block resident at once (bounded by the occupancy)
   int per_sm = 0, coop = 0, dev = 0;
@@ -646,7 +657,7 @@ int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ld
     }
   }
   for (int64_t sweep = 1; sweep <= max_sweeps; ++sweep) {
-    FTT_CUDA(cudaMemsetAsync(rot.get(), 0, 4 * sizeof(unsigned), s));
+    reset_rot();
     KClock clk;
     kclock_begin(clk, f64 ? KC_JACOBI : KC_JACOBI32, s);
     bool done = false;
@@ -666,12 +677,12 @@ int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ld
         FTT_CUDA(cudaMemcpyAsync(h, rot.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
         FTT_CUDA(cudaStreamSynchronize(s));
         if (h[3] == 0) done = true;
-        else bj = 0;
+        else { barrier_gave_up(); bj = 0; }
       } else {
         cudaGetLastError();
         bj = 0;
       }
-      if (!done) FTT_CUDA(cudaMemsetAsync(rot.get(), 0, 4 * sizeof(unsigned), s));
+      if (!done) reset_rot();
     }
     if (!done && use_coop) {
       unsigned* rp = rot.get();
@@ -685,12 +696,12 @@ int64_t jacobi(T* A, int64_t m, int64_t lda, int n, T* V, int64_t nv, int64_t ld
         FTT_CUDA(cudaMemcpyAsync(h, rot.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
         FTT_CUDA(cudaStreamSynchronize(s));
         if (h[3] == 0) done = true;       // no barrier timed out
-        else use_coop = false;            // redo this sweep round by round
+        else { barrier_gave_up(); use_coop = false; }   // redo this sweep round by round
       } else {
         cudaGetLastError();
         use_coop = false;
       }
-      if (!done) FTT_CUDA(cudaMemsetAsync(rot.get(), 0, 4 * sizeof(unsigned), s));
+      if (!done) reset_rot();
     }
     if (!done) {
       for (int round = 0; round < n2 - 1; ++round) {

@@ -34,6 +34,8 @@ bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const
                 int64_t scj, cudaStream_t s, bool sym = false);
 
 void ozaki_take_timeout(cudaStream_t s);
+// Reads and clears the sticky flag without throwing; true if it was set.
+bool ozaki_clear_timeout(cudaStream_t s);
 
 // Products below this many multiply-adds stay on the DFMA / mma.sync kernels.
 constexpr double kTensorGemmMin = 67108864.0;   // 2^26

@@ -30,10 +30,20 @@ __device__ __forceinline__ void block_sum3(T& a, T& b, T& c) {
 }
 
 // Grid-wide barrier of a cooperative launch (all blocks co-resident).  bar[0]
-// counts arrivals, bar[1] is the generation, bar[2] an error flag.  The wait is
-// bounded: after kBarrierSpins polls the block raises the error flag and every
-// block leaves the kernel at its next barrier.
+// counts arrivals, bar[1] is the generation, bar[2] an error flag, bar[3] the poll
+// bound (0: kBarrierSpins).  The wait is bounded: after that many polls the block
+// raises the error flag and every block leaves the kernel at its next barrier.
 constexpr long long kBarrierSpins = 1ll << 24;
+
+// bar[0..2] = 0, bar[3] = the poll bound (set before every cooperative launch)
+__global__ void barrier_init_kernel(unsigned* bar, unsigned spins) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    bar[0] = 0u;
+    bar[1] = 0u;
+    bar[2] = 0u;
+    bar[3] = spins;
+  }
+}
 
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen) {
   __shared__ int ok;
@@ -50,9 +60,10 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen) {
       atomicAdd(bar + 1, 1u);
     } else {
       long long it = 0;
+      const long long limit = bar[3] ? (long long)bar[3] : kBarrierSpins;
       while (*vgen == gen) {
         if (*verr) { ok = 0; break; }
-        if (++it > kBarrierSpins) { atomicOr(bar + 2, 1u); ok = 0; break; }
+        if (++it > limit) { atomicOr(bar + 2, 1u); ok = 0; break; }
         __nanosleep(64);
       }
     }

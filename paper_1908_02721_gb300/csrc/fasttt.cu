@@ -66,6 +66,22 @@ namespace {
 thread_local int g_gemm_engine = 0;
 }
 void set_gemm_engine(int engine) { g_gemm_engine = engine; }
+namespace {
+thread_local int64_t g_max_spin = 0;
+std::atomic<int64_t> g_wait_timeouts{0};
+}  // namespace
+void set_max_spin(int64_t spins) { g_max_spin = spins > 0 ? spins : 0; }
+namespace {
+// The calling thread's poll bound for the duration of one call, back to the
+// defaults afterwards (so that later calls without the option are not bounded).
+struct MaxSpinScope {
+  explicit MaxSpinScope(int64_t spins) { set_max_spin(spins); }
+  ~MaxSpinScope() { set_max_spin(0); }
+};
+}  // namespace
+int64_t max_spin() { return g_max_spin; }
+void note_wait_timeout() { g_wait_timeouts.fetch_add(1, std::memory_order_relaxed); }
+int64_t wait_timeouts() { return g_wait_timeouts.load(); }
 int gemm_engine() { return g_gemm_engine; }
 void note_eig(bool tridiag) { (tridiag ? g_eig_tridiag : g_eig_fallback).fetch_add(1, std::memory_order_relaxed); }
 void note_eig_fast() { g_eig_fast.fetch_add(1, std::memory_order_relaxed); }
@@ -210,6 +226,7 @@ __global__ void place_block_kernel(const double* src, int64_t r0, int64_t n, int
 
 struct Handle {
   int d = 0;
+  int64_t wait0 = wait_timeouts();   // device waits given up before this call
   std::vector<int64_t> dims, ranks;
   std::vector<DBuf<double>> cores;
   fasttt_stats st{};
@@ -373,6 +390,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   if (o.gemm_engine != FASTTT_GEMM_TENSOR && o.gemm_engine != FASTTT_GEMM_DFMA)
     fail(FASTTT_EINVAL, "bad gemm_engine");
   set_gemm_engine(o.gemm_engine);
+  MaxSpinScope spin_scope(o.max_spin);
   const int64_t max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
   fasttt_stats& st = H.st;
   st.d = d;
@@ -696,6 +714,7 @@ void round_tt(int d, const int64_t* dims, const int64_t* ranks, const double* co
   if (o.gemm_engine != FASTTT_GEMM_TENSOR && o.gemm_engine != FASTTT_GEMM_DFMA) fail(FASTTT_EINVAL, "bad gemm_engine");
   if (o.max_rank < 0) fail(FASTTT_EINVAL, "max_rank must be >= 0");
   set_gemm_engine(o.gemm_engine);
+  MaxSpinScope spin_scope(o.max_spin);
   const bool mixed = (o.precision == FASTTT_PREC_MIXED);
   const bool eps0 = (eps == 0.0);
   const int64_t max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 40;
@@ -825,6 +844,22 @@ int handle_error(const Error& e) {
   return e.code;
 }
 
+// A call that failed after a tensor-core GEMM gave up on a bounded wait computed on
+// that GEMM's unfinished output: report the give-up (ETIMEOUT) as the cause, and
+// clear the sticky flag so that it does not fail the next call.
+int timeout_as_cause(int rc, cudaStream_t s) {
+  if (rc == FASTTT_ETIMEOUT) {
+    ozaki_clear_timeout(s);
+    return rc;
+  }
+  if (ozaki_clear_timeout(s)) {
+    g_last_error = "tensor-core GEMM: a bounded wait gave up (then: " + g_last_error + ")";
+    note_wait_timeout();
+    return FASTTT_ETIMEOUT;
+  }
+  return rc;
+}
+
 }  // namespace
 
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
@@ -854,11 +889,13 @@ int make_handle(void* stream, fasttt_tt** out, fasttt_stats* stats, F&& body) {
     g_last_error = e.what();
     rc = FASTTT_ECUDA;
   }
-  if (stats) *stats = tt->h.st;
   if (rc != FASTTT_OK) {
     cudaStreamSynchronize(s);
-    return rc;
+    rc = timeout_as_cause(rc, s);
   }
+  tt->h.st.wait_timeouts = wait_timeouts() - tt->h.wait0;
+  if (stats) *stats = tt->h.st;
+  if (rc != FASTTT_OK) return rc;
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     g_last_error = std::string("CUDA error: ") + cudaGetErrorString(e);
@@ -907,11 +944,13 @@ int fasttt_decompose(int d, const int64_t* dims, int64_t nnz, const int32_t* d_i
     g_last_error = e.what();
     rc = FASTTT_ECUDA;
   }
-  if (stats) *stats = tt->h.st;
   if (rc != FASTTT_OK) {
     cudaStreamSynchronize(s);
-    return rc;
+    rc = timeout_as_cause(rc, s);
   }
+  tt->h.st.wait_timeouts = wait_timeouts() - tt->h.wait0;
+  if (stats) *stats = tt->h.st;
+  if (rc != FASTTT_OK) return rc;
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     g_last_error = std::string("CUDA error: ") + cudaGetErrorString(e);

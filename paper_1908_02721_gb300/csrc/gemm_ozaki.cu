@@ -59,8 +59,8 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kMbarSpins; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long spins = kMbarSpins) {
+  for (long long it = 0; it < spins; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     ozaki_gemm_kernel(const __nv_bfloat16* __restrict__ qa, const __nv_bfloat16* __restrict__ qb, int64_t M,
                       int64_t N, int64_t Kp, int64_t Mp, int64_t Np, const int* __restrict__ ea,
                       const int* __restrict__ fb, double alpha, double beta, double* __restrict__ C, int64_t sci,
-                      int64_t scj, bool sym) {
+                      int64_t scj, bool sym, long long spins) {
   static_assert((long long)KD * oz_level_max<S, BITS>() < (1ll << 24), "level sums of a window must stay exact");
   static_assert(KD % kBKs == 0, "windows are whole stages");
   static_assert(S * BN <= 512 && BN % 64 == 0, "the level accumulators must fit TMEM");
@@ -233,14 +233,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int q = 0; q < NST; ++q) { tma_pending[q] = false; tma_phase[q] = 0; empty_phase[q] = 0; }
   if (tid == 0)
     for (int st = 0; st < NST && st < nk; ++st) { load_stage(st, st); tma_pending[st] = true; }
-  bool ok = true;
+  bool ok = true, drain_pending = false;
   uint32_t drain_phase = 0;
   for (int w0 = 0; w0 < nk; w0 += kWindow) {
     const int w1 = (w0 + kWindow < nk) ? w0 + kWindow : nk;
     if (tid == 0 && !abort_flag) {
       for (int kc = w0; kc < w1; ++kc) {
         const int st = kc % NST;
-        if (!mbar_wait(&full_bar[st], tma_phase[st])) { abort_flag = 1; break; }
+        if (!mbar_wait(&full_bar[st], tma_phase[st], spins)) { abort_flag = 1; break; }
         tma_pending[st] = false;
         tma_phase[st] ^= 1;
         tc_fence_after();
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // refill the stage of step kc - 1 (its MMAs run ahead of these) with step kc - 1 + NST
         if (kc >= 1 && kc - 1 + NST < nk) {
           const int o = (kc - 1) % NST;
-          if (!mbar_wait(&empty_bar[o], empty_phase[o])) { abort_flag = 1; break; }
+          if (!mbar_wait(&empty_bar[o], empty_phase[o], spins)) { abort_flag = 1; break; }
           empty_phase[o] ^= 1;
           load_stage(o, kc - 1 + NST);
           tma_pending[o] = true;
@@ -275,8 +275,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!abort_flag) umma_commit(&drain_bar);
     }
+    // the issuing thread gave up (its pipeline waits use the caller's bound): no drain
+    // commit was made for this window; the abort path below waits for what is in flight
+    if (__syncthreads_or(abort_flag)) { ok = false; break; }
     const bool got = mbar_wait(&drain_bar, drain_phase);
-    if (__syncthreads_or(!got || abort_flag)) { ok = false; break; }
+    if (__syncthreads_or(!got)) {   // the window's commit is still outstanding
+      drain_pending = true;
+      ok = false;
+      break;
+    }
     drain_phase ^= 1;
     tc_fence_after();
     // drain: TMEM lanes 32 * quarter .. (tile rows), columns kCPT * half .. of every level
@@ -322,7 +329,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
       for (int st = 0; st < NST; ++st)
         if (tma_pending[st]) mbar_wait(&full_bar[st], tma_phase[st]);
+      // one commit after every MMA issued: wait for it (and for the window's own commit
+      // first, if that one is still outstanding), so no arrive lands after the exit
       umma_commit(&drain_bar);
+      if (drain_pending) {
+        mbar_wait(&drain_bar, drain_phase);
+        drain_phase ^= 1;
+      }
       mbar_wait(&drain_bar, drain_phase);
       atomicOr(&g_oz_timeout, 1);
     }
@@ -526,7 +539,7 @@ bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
   kclock_begin(clk, KC_GEMM_OZ, s);
   ozaki_gemm_kernel<S, BITS, KD, BN, NST><<<dim3((unsigned)(Mp / kBM), (unsigned)(Np / BN)), kThreads, smem, s>>>(
       qa.get(), same ? qa.get() : qb.get(), M, N, Kp, Mp, same ? Mp : Np, ea.get(), same ? ea.get() : fb.get(), alpha,
-      beta, C, sci, scj, sym);
+      beta, C, sci, scj, sym, max_spin() > 0 ? (long long)max_spin() : kMbarSpins);
   FTT_LAUNCH();
   kclock_end(clk, (sym ? 1.0 : 2.0) * (double)M * (double)N * (double)K, s);
   if (sym) {
@@ -546,8 +559,25 @@ void ozaki_take_timeout(cudaStream_t s) {
   if (h) {
     FTT_CUDA(cudaMemcpyToSymbolAsync(g_oz_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
     FTT_CUDA(cudaStreamSynchronize(s));
+    note_wait_timeout();
     fail(FASTTT_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up");
   }
+}
+
+bool ozaki_clear_timeout(cudaStream_t s) {
+  int h = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_oz_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (h) {
+    cudaMemcpyToSymbolAsync(g_oz_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+  }
+  return h != 0;
 }
 
 bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t sai, int64_t sak,

@@ -574,7 +574,8 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
     const int grid = std::min(2, per) * sms;
     if (grid < 1) return false;
     DBuf<unsigned> bar(4, s);
-    FTT_CUDA(cudaMemsetAsync(bar.get(), 0, 4 * sizeof(unsigned), s));
+    barrier_init_kernel<<<1, 1, 0, s>>>(bar.get(), barrier_spins());
+    FTT_LAUNCH();
     int64_t n64 = n;
     double *Ap = A.get(), *dp = d.get(), *ep = e.get(), *tp = tau.get(), *pp = p.get();
     unsigned* bp = bar.get();
@@ -592,7 +593,11 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
     unsigned hb[4];
     FTT_CUDA(cudaMemcpyAsync(hb, bar.get(), sizeof(hb), cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
-    if (hb[2] != 0) return false;
+    if (hb[2] != 0) {   // a grid barrier gave up: fail with an explicit bound, else the next route
+      note_wait_timeout();
+      if (max_spin() > 0) fail(FASTTT_ETIMEOUT, "a grid barrier of the tridiagonalisation exceeded max_spin polls");
+      return false;
+    }
   }
   std::vector<double> hd(n), he(n);
   FTT_CUDA(cudaMemcpyAsync(hd.data(), d.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -716,7 +721,8 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     const int grid = std::min(2, per) * sms;
     if (grid < 1) return false;
     DBuf<unsigned> bar(4, s);
-    FTT_CUDA(cudaMemsetAsync(bar.get(), 0, 4 * sizeof(unsigned), s));
+    barrier_init_kernel<<<1, 1, 0, s>>>(bar.get(), barrier_spins());
+    FTT_LAUNCH();
     int64_t n64 = n;
     float *Ap = A.get(), *dp = d.get(), *ep = e.get(), *tp = tau.get(), *pp = p.get();
     unsigned* bp = bar.get();
@@ -734,7 +740,11 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     unsigned hb[4];
     FTT_CUDA(cudaMemcpyAsync(hb, bar.get(), sizeof(hb), cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
-    if (hb[2] != 0) return false;
+    if (hb[2] != 0) {   // a grid barrier gave up: fail with an explicit bound, else the next route
+      note_wait_timeout();
+      if (max_spin() > 0) fail(FASTTT_ETIMEOUT, "a grid barrier of the tridiagonalisation exceeded max_spin polls");
+      return false;
+    }
   }
   std::vector<float> hd(n), he(n);
   FTT_CUDA(cudaMemcpyAsync(hd.data(), d.get(), sizeof(float) * n, cudaMemcpyDeviceToHost, s));
