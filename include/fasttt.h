@@ -65,13 +65,16 @@ extern "C" {
 /* fasttt_opts.stage */
 #define FASTTT_STAGE_FULL 0  /* Alg. 7: exact TT, then TT-rounding */
 #define FASTTT_STAGE_EXACT 1 /* Alg. 4 only: the lossless exact sparse TT (no cores) */
+#define FASTTT_STAGE_DEPAR 2 /* Alg. 4 and the value Depar of the middle unfolding (Alg. 3), no
+                                rounding: the grouping and Depar factors of tensors whose exact
+                                ranks are too large to round (intermediates always kept) */
 
 typedef struct fasttt_opts {
   int p;              /* split point 1..d; 0 = choose by Alg. 9 (flop model, eq. (13)) */
   int precision;      /* FASTTT_PREC_FP64 or FASTTT_PREC_MIXED */
   int rounding;       /* FASTTT_STATIC or FASTTT_DYNAMIC */
   int depar_values;   /* 1: value Depar (Alg. 3, exact parallelism) of the middle unfolding; 0: off */
-  int stage;          /* FASTTT_STAGE_FULL or FASTTT_STAGE_EXACT */
+  int stage;          /* FASTTT_STAGE_FULL, FASTTT_STAGE_EXACT or FASTTT_STAGE_DEPAR */
   int keep_intermediates; /* 1: keep group maps, middle COO, Depar factors, singular values */
   int64_t max_rank;   /* > 0: cap every TT rank (fixed-rank variant, Sec. 3.4); 0: none */
   int64_t max_sweeps; /* Jacobi sweep bound of the dense SVDs; 0 = default (40) */

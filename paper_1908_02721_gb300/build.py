@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfasttt.so")
-SOURCES = ["prims.cu", "group.cu", "depar.cu", "dense.cu", "chol.cu", "tridiag.cu", "gemm_ozaki.cu", "tsqr.cu", "sparse_sweep.cu", "gemm_tc.cu", "tteval.cu", "fasttt.cu",
+SOURCES = ["prims.cu", "group.cu", "depar.cu", "dense.cu", "chol.cu", "tridiag.cu", "gemm_ozaki.cu", "tsqr.cu", "sparse_sweep.cu", "gemm_tc.cu", "tteval.cu", "tteval_sorted.cu", "fasttt.cu",
            "noalloc.cu", "ttfit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

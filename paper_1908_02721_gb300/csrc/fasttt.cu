@@ -384,7 +384,8 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   if (o.rounding != FASTTT_STATIC && o.rounding != FASTTT_DYNAMIC) fail(FASTTT_EINVAL, "bad rounding mode");
   if (o.precision != FASTTT_PREC_FP64 && o.precision != FASTTT_PREC_MIXED) fail(FASTTT_EINVAL, "unsupported precision");
   const bool mixed = (o.precision == FASTTT_PREC_MIXED);
-  if (o.stage != FASTTT_STAGE_FULL && o.stage != FASTTT_STAGE_EXACT) fail(FASTTT_EINVAL, "bad stage");
+  if (o.stage != FASTTT_STAGE_FULL && o.stage != FASTTT_STAGE_EXACT && o.stage != FASTTT_STAGE_DEPAR)
+    fail(FASTTT_EINVAL, "bad stage");
   if (o.sparse_sweep < FASTTT_SWEEP_AUTO || o.sparse_sweep > FASTTT_SWEEP_DENSE)
     fail(FASTTT_EINVAL, "bad sparse_sweep mode");
   if (o.gemm_engine != FASTTT_GEMM_TENSOR && o.gemm_engine != FASTTT_GEMM_DFMA)
@@ -433,6 +434,14 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
   st.beta_r = dp.rows.beta;
   st.beta_c = dp.cols.beta;
   st.ms_depar = lap.lap();
+  if (o.stage == FASTTT_STAGE_DEPAR) {
+    H.kept = true;
+    for (int k = 0; k <= d; ++k) st.ranks[k] = g.rt[k];
+    H.ranks.assign(g.rt.begin(), g.rt.end());
+    st.ms_total = total.lap();
+    finish_stats(st, launches0);
+    return;
+  }
 
   // S7-S11
   const std::vector<int64_t>& n = H.dims;

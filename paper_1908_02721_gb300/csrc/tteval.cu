@@ -20,6 +20,15 @@
 #include "common.cuh"
 
 namespace fasttt {
+
+// The index-sorted batched path (tteval_sorted.cu) for ranks 16..1024.
+bool tteval_sorted_applies(int d, const int64_t* dims, const int64_t* ranks);
+void tt_eval_sorted(int d, const int64_t* dims, const int64_t* ranks, const void* const* cores, int dtype, int64_t m,
+                    const int32_t* idx, void* out, cudaStream_t s);
+void tt_backward_sorted(int d, const int64_t* dims, const int64_t* ranks, const void* const* cores, int dtype,
+                        int64_t m, const int32_t* idx, const void* gout, void* const* grads, int recompute,
+                        cudaStream_t s);
+
 namespace {
 
 constexpr int kMaxWarps = 8;            // warps per block at most
@@ -256,6 +265,10 @@ int tt_eval_at_impl(int d, const int64_t* dims, const int64_t* ranks, const void
   check_args(d, dims, ranks, cores, dtype, m, idx, ca);
   if (m == 0) return FASTTT_OK;
   if (!out) fail(FASTTT_EINVAL, "null output");
+  if (!small_shape(ca, d) && tteval_sorted_applies(d, dims, ranks)) {
+    tt_eval_sorted(d, dims, ranks, cores, dtype, m, idx, out, s);
+    return FASTTT_OK;
+  }
   DBuf<unsigned> err(1, s);
   FTT_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(unsigned), s));
   const int rmax = max_rank_of(ca, d);
@@ -292,6 +305,10 @@ int tt_eval_backward_impl(int d, const int64_t* dims, const int64_t* ranks, cons
   }
   if (m == 0) return FASTTT_OK;
   if (!gout) fail(FASTTT_EINVAL, "null upstream gradient");
+  if (tteval_sorted_applies(d, dims, ranks)) {
+    tt_backward_sorted(d, dims, ranks, cores, dtype, m, idx, gout, grads, recompute, s);
+    return FASTTT_OK;
+  }
   DBuf<unsigned> err(1, s);
   FTT_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(unsigned), s));
   const int rmax = max_rank_of(ca, d);

@@ -25,7 +25,8 @@ OK, EINVAL, EDUP, ENOMEM, ETIMEOUT, ENUMERIC, ERANK, ECUDA = 0, -1, -2, -3, -4, 
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STATIC, DYNAMIC = 0, 1
-STAGE_FULL, STAGE_EXACT = 0, 1
+STAGE_FULL, STAGE_EXACT, STAGE_DEPAR = 0, 1, 2
+STAGES = {"full": STAGE_FULL, "exact": STAGE_EXACT, "depar": STAGE_DEPAR}
 SWEEP_MODES = {"auto": 0, "sparse": 1, "dense": 2}
 GEMM_ENGINES = {"tensor": 0, "dfma": 1}
 ARR = {name: i for i, name in enumerate([
@@ -365,7 +366,9 @@ def fasttt_decompose(idx, vals, dims, eps, *, p=0, max_rank=0, depar_values=True
     o.max_rank = int(max_rank)
     o.depar_values = 1 if depar_values else 0
     o.rounding = DYNAMIC if rounding == "dynamic" else STATIC
-    o.stage = STAGE_EXACT if stage == "exact" else STAGE_FULL
+    if stage not in STAGES:
+        raise FastTTError(EINVAL, "stage must be 'full', 'exact' or 'depar'")
+    o.stage = STAGES[stage]
     o.keep_intermediates = 1 if keep_intermediates else 0
     o.max_sweeps = int(max_sweeps)
     o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
