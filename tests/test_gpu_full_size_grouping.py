@@ -9,8 +9,8 @@ workloads, against the oracle (S2-S6: Alg. 4 with Alg. 5, Alg. 3):
 
 These sizes take wider keys (more radix passes) and r~ in the millions.  Group
 maps, r~, R, the middle unfolding's COO, Depar classes, prefactors and D' must be
-equal bit for bit; Lambda (an exactly rounded sum in the oracle, a pairwise tree
-on the GPU) within the tree's error bound for each class's size.  The oracle
+equal bit for bit; Lambda (an exactly rounded sum in the oracle, a sequential
+sum on the GPU) within that sum's error bound for each class's size.  The oracle
 takes a few minutes here.
 """
 import numpy as np
@@ -61,12 +61,13 @@ def _check(F, w, p):
     assert np.array_equal(g_r[o1], dp.dp_rows[o2])
     assert np.array_equal(g_c[o1], dp.dp_cols[o2])
     assert np.array_equal(g_v[o1], dp.dp_vals[o2])
-    # Lambda: the oracle's sum of squares is exactly rounded, the GPU's a pairwise tree of
-    # K squares (relative error <= ceil(log2 K) u); the square root halves it and adds u/2
+    # Lambda: the oracle's sum of squares is exactly rounded, the GPU's a sequential FMA sum
+    # of a class's K squares in ascending member order (relative error <= (K - 1) u for
+    # positive terms); the square root halves it and adds u / 2
     for name, lam, cls, beta in (("lam_s", dp.lam_s, dp.row_class, dp.beta_r),
                                  ("lam_t", dp.lam_t, dp.col_class, dp.beta_c)):
         size = np.bincount(cls, minlength=beta)
-        bound = (0.5 * np.ceil(np.log2(np.maximum(size, 1))) + 1.0) * 2.0 ** -53
+        bound = (0.5 * np.maximum(size - 1, 0) + 1.0) * 2.0 ** -53
         got = _np(tt.array(name))
         assert np.all(np.abs(got - lam) <= bound * lam), name
     tt.free()
