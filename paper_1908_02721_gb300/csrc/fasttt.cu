@@ -34,11 +34,43 @@ thread_local std::string g_last_error;
 thread_local bool g_free_sync = false;
 }  // namespace
 
+namespace {
+// Once per device: let the device's default memory pool (the one cudaMallocAsync
+// draws from) keep up to a quarter of the device's memory cached across stream
+// synchronisations instead of returning every freed block to the driver, so that
+// the library's per-call work buffers are not mapped again on every call.  This is
+// a setting of this process's pool (it ends with the process), not of the GPU.
+constexpr int kPoolDevices = 64;
+std::atomic<bool> g_pool_set[kPoolDevices];
+
+void configure_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kPoolDevices) {
+    cudaGetLastError();
+    return;
+  }
+  if (g_pool_set[dev].exchange(true)) return;
+  cudaMemPool_t pool;
+  size_t fr = 0, tot = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess || cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  uint64_t threshold = (uint64_t)tot / 4;
+  uint64_t current = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &current) == cudaSuccess &&
+      current < threshold)
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  cudaGetLastError();
+}
+}  // namespace
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     if (g_fail_after > 0 && --g_fail_after == 0) fail(FASTTT_ENOMEM, "injected allocation failure");
   }
+  configure_pool();
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, bytes, s);
   if (e != cudaSuccess) {

@@ -65,76 +65,113 @@ __global__ void runs_kernel(const uint64_t* keys, int64_t m, int32_t* key32, int
   }
 }
 
-// Out[perm[j], c] = sum_a A[perm[j], a] Bi(a, c) for the 64 sorted rows j of this
+// four consecutive shared-memory values (16-byte aligned) as one or two vector loads
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+constexpr int kGM = 128;   // sorted rows per propagation tile (8 per thread), kTN columns (4 per thread)
+
+// Out[perm[j], c] = sum_a A[perm[j], a] Bi(a, c) for the kGM sorted rows j of this
 // tile, Bi the matrix of row j's index i = key[j]: Bi(a, c) = G[i s_i + a s_k + c s_c].
 // A: m x K row-major (a_ones: K = 1 and A = 1).  Out: m x N row-major.  Runs of equal
 // keys inside the tile are contracted one after the other (rows outside the run
-// contribute zeros).
+// contribute zeros).  The next K step's gathered values are loaded into registers
+// while the current step is multiplied.
 template <typename T>
 __global__ void __launch_bounds__(256) gathered_gemm_kernel(const T* __restrict__ A, bool a_ones, int K,
                                                             const T* __restrict__ G, int64_t s_i, int64_t s_k,
                                                             int64_t s_c, int N, const uint32_t* __restrict__ perm,
                                                             const int32_t* __restrict__ key, int64_t m,
                                                             T* __restrict__ Out) {
-  __shared__ T As[kTK][kTM + 1];
-  __shared__ T Bs[kTK][kTN + 1];
-  __shared__ uint32_t rows[kTM];
-  __shared__ int32_t keys[kTM];
-  const int64_t j0 = (int64_t)blockIdx.x * kTM;
+  __shared__ __align__(16) T As[kTK][kGM + 4];
+  __shared__ __align__(16) T Bs[kTK][kTN + 4];
+  __shared__ uint32_t rows[kGM];
+  __shared__ int32_t keys[kGM];
+  const int64_t j0 = (int64_t)blockIdx.x * kGM;
   const int c0 = blockIdx.y * kTN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int nrow = (int)min((int64_t)kTM, m - j0);
-  if (threadIdx.x < kTM) {
+  const int nrow = (int)min((int64_t)kGM, m - j0);
+  if (threadIdx.x < kGM) {
     const bool in = threadIdx.x < nrow;
     rows[threadIdx.x] = in ? perm[j0 + threadIdx.x] : 0u;
     keys[threadIdx.x] = in ? key[j0 + threadIdx.x] : -1;
   }
   __syncthreads();
-  T acc[4][4];
+  T acc[8][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
   const bool b_k_fast = (s_k == 1);
+  // this thread's share of a K step: 8 A values (rows e / kTK, k e % kTK), 4 B values
+  T ra[8], rb[4];
   for (int rs = 0; rs < nrow;) {
     const int kc = keys[rs];
     int re = rs + 1;
     while (re < nrow && keys[re] == kc) ++re;
     const T* Gi = G + (int64_t)kc * s_i;
-    for (int a0 = 0; a0 < K; a0 += kTK) {
-      for (int e = threadIdx.x; e < kTM * kTK; e += 256) {
+    auto fetch = [&](int a0) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int e = threadIdx.x + t * 256;
         const int row = e / kTK, kk = e % kTK;
         T v = T(0);
         if (row >= rs && row < re && a0 + kk < K) v = a_ones ? T(1) : A[(int64_t)rows[row] * K + a0 + kk];
-        As[kk][row] = v;
+        ra[t] = v;
       }
-      for (int e = threadIdx.x; e < kTK * kTN; e += 256) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = threadIdx.x + t * 256;
         int kk, cc;
         if (b_k_fast) { kk = e % kTK; cc = e / kTK; } else { kk = e / kTN; cc = e % kTN; }
         T v = T(0);
         if (a0 + kk < K && c0 + cc < N) v = Gi[(int64_t)(a0 + kk) * s_k + (int64_t)(c0 + cc) * s_c];
-        Bs[kk][cc] = v;
+        rb[t] = v;
+      }
+    };
+    fetch(0);
+    for (int a0 = 0; a0 < K; a0 += kTK) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int e = threadIdx.x + t * 256;
+        As[e % kTK][e / kTK] = ra[t];
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = threadIdx.x + t * 256;
+        if (b_k_fast) Bs[e % kTK][e / kTK] = rb[t];
+        else Bs[e / kTN][e % kTN] = rb[t];
       }
       __syncthreads();
+      if (a0 + kTK < K) fetch(a0 + kTK);   // the next step's loads fly during the products
 #pragma unroll
       for (int kk = 0; kk < kTK; ++kk) {
-        T av[4], bv[4];
+        T av0[4], av1[4], bv[4];
+        ld4(&As[kk][ty * 8], av0);
+        ld4(&As[kk][ty * 8 + 4], av1);
+        ld4(&Bs[kk][tx * 4], bv);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+        for (int j = 0; j < 4; ++j) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+          for (int i = 0; i < 4; ++i) {
+            acc[i][j] = fma(av0[i], bv[j], acc[i][j]);
+            acc[i + 4][j] = fma(av1[i], bv[j], acc[i + 4][j]);
+          }
+        }
       }
       __syncthreads();
     }
     rs = re;
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = ty * 4 + i;
+  for (int i = 0; i < 8; ++i) {
+    const int row = ty * 8 + i;
     if (row >= nrow) continue;
     T* o = Out + (int64_t)rows[row] * N;
 #pragma unroll
@@ -147,17 +184,16 @@ __global__ void __launch_bounds__(256) gathered_gemm_kernel(const T* __restrict_
 
 // partial[ch] (r0 x r1, this block's 64 x 64 tile of it) = sum over the sorted
 // positions j in [lo[ch], hi[ch]) of g[perm j] L[perm j]^T R[perm j]
-// (l_ones: r0 = 1, L = 1; r_ones: r1 = 1, R = 1)
+// (l_ones: r0 = 1, L = 1; r_ones: r1 = 1, R = 1).  The next step's gathered rows are
+// loaded into registers while the current step is multiplied.
 template <typename T>
 __global__ void __launch_bounds__(256) grad_chunk_kernel(const T* __restrict__ L, bool l_ones, int r0,
                                                          const T* __restrict__ R, bool r_ones, int r1,
                                                          const T* __restrict__ g, const uint32_t* __restrict__ perm,
                                                          const int64_t* __restrict__ lo,
                                                          const int64_t* __restrict__ hi, T* __restrict__ partial) {
-  __shared__ T Ls[kTK][kTM + 1];
-  __shared__ T Rs[kTK][kTN + 1];
-  __shared__ uint32_t ent[kTK];
-  __shared__ T gw[kTK];
+  __shared__ __align__(16) T Ls[kTK][kTM + 4];
+  __shared__ __align__(16) T Rs[kTK][kTN + 4];
   const int ch = blockIdx.x;
   const int a0 = blockIdx.y * kTM, c0 = blockIdx.z * kTN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -167,35 +203,39 @@ __global__ void __launch_bounds__(256) grad_chunk_kernel(const T* __restrict__ L
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  // this thread's share of a step: 4 L values and 4 R values (entry q / 64, column q % 64)
+  T rl[4], rr[4];
+  auto fetch = [&](int64_t j0) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int q = threadIdx.x + t * 256;
+      const int kk = q / kTM, col = q % kTM;
+      const int64_t j = j0 + kk;
+      T lv = T(0), rv = T(0);
+      if (j < j_hi) {
+        const uint32_t e = perm[j];
+        if (a0 + col < r0) lv = l_ones ? T(1) : L[(int64_t)e * r0 + a0 + col];
+        if (c0 + col < r1) rv = g[e] * (r_ones ? T(1) : R[(int64_t)e * r1 + c0 + col]);
+      }
+      rl[t] = lv;
+      rr[t] = rv;
+    }
+  };
+  fetch(j_lo);
   for (int64_t j0 = j_lo; j0 < j_hi; j0 += kTK) {
-    if (threadIdx.x < kTK) {
-      const int64_t j = j0 + threadIdx.x;
-      const bool in = j < j_hi;
-      const uint32_t e = in ? perm[j] : 0u;
-      ent[threadIdx.x] = e;
-      gw[threadIdx.x] = in ? g[e] : T(0);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int q = threadIdx.x + t * 256;
+      Ls[q / kTM][q % kTM] = rl[t];
+      Rs[q / kTN][q % kTN] = rr[t];
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < kTK * kTM; q += 256) {
-      const int kk = q / kTM, a = q % kTM;
-      T v = T(0);
-      if (j0 + kk < j_hi && a0 + a < r0) v = l_ones ? T(1) : L[(int64_t)ent[kk] * r0 + a0 + a];
-      Ls[kk][a] = v;
-    }
-    for (int q = threadIdx.x; q < kTK * kTN; q += 256) {
-      const int kk = q / kTN, c = q % kTN;
-      T v = T(0);
-      if (j0 + kk < j_hi && c0 + c < r1) v = gw[kk] * (r_ones ? T(1) : R[(int64_t)ent[kk] * r1 + c0 + c]);
-      Rs[kk][c] = v;
-    }
-    __syncthreads();
+    if (j0 + kTK < j_hi) fetch(j0 + kTK);
 #pragma unroll
     for (int kk = 0; kk < kTK; ++kk) {
       T av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = Ls[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Rs[kk][tx * 4 + j];
+      ld4(&Ls[kk][ty * 4], av);
+      ld4(&Rs[kk][tx * 4], bv);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -266,7 +306,7 @@ void sort_mode(const int32_t* idx_k, int64_t mc, int32_t n, ModeOrder& mo, uint6
 template <typename T>
 void propagate(const T* A, bool a_ones, int K, const T* G, int64_t s_i, int64_t s_k, int64_t s_c, int N,
                const ModeOrder& mo, int64_t mc, T* Out, cudaStream_t s) {
-  const dim3 grid((unsigned)ceil_div(mc, kTM), (unsigned)ceil_div(N, kTN));
+  const dim3 grid((unsigned)ceil_div(mc, kGM), (unsigned)ceil_div(N, kTN));
   gathered_gemm_kernel<T><<<grid, 256, 0, s>>>(A, a_ones, K, G, s_i, s_k, s_c, N, mo.perm.get(), mo.key.get(), mc,
                                                Out);
   FTT_LAUNCH();
@@ -318,7 +358,7 @@ void gradient(const T* L, bool l_ones, int r0, const T* R, bool r_ones, int r1, 
   grad_reduce_kernel<T><<<grid_for(nb * r0 * r1), 256, 0, s>>>(partial.get(), r0, r1, n, nb, dbucket.get(),
                                                                 dfirst.get(), dcount.get(), dG);
   FTT_LAUNCH();
-  FTT_CUDA(cudaStreamSynchronize(s));   // the host vectors above are read by the copies
+  // the host vectors above were staged by the copies (pageable sources) before they returned
 }
 
 void check_indices(int d, const int64_t* dims, int64_t m, const int32_t* idx, cudaStream_t s) {
