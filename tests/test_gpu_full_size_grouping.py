@@ -63,11 +63,11 @@ def _check(F, w, p):
     assert np.array_equal(g_v[o1], dp.dp_vals[o2])
     # Lambda: the oracle's sum of squares is exactly rounded, the GPU's a sequential FMA sum
     # of a class's K squares in ascending member order (relative error <= (K - 1) u for
-    # positive terms); the square root halves it and adds u / 2
+    # positive terms); the square root halves it, and each side rounds its square root (u each)
     for name, lam, cls, beta in (("lam_s", dp.lam_s, dp.row_class, dp.beta_r),
                                  ("lam_t", dp.lam_t, dp.col_class, dp.beta_c)):
         size = np.bincount(cls, minlength=beta)
-        bound = (0.5 * np.maximum(size - 1, 0) + 1.0) * 2.0 ** -53
+        bound = (0.5 * np.maximum(size - 1, 0) + 2.0) * 2.0 ** -53
         got = _np(tt.array(name))
         assert np.all(np.abs(got - lam) <= bound * lam), name
     tt.free()
