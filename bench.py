@@ -44,6 +44,12 @@ HEADLINE_M = 12                                     # 2^12 x 2^12 banded matrix,
 SAMPLE_M = 10                                       # oracle sample: the same recipe at 2^10 x 2^10
 OZ_PAIRS_FP64 = 36                                  # slice pairs (s, t), s + t <= 9, of the 8-slice product
 ERR_BAR = 1e-6                                      # the metric's relative-error bar
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the headline step's
+# kernels, from one ncu capture of the headline decomposition (profiles/ has the summary and
+# the command); a kernel changed since the capture has no entry
+NCU_TRAFFIC = {
+    "tridiag_kernel<double>": {"bytes": 168.55e9, "source": "ncu, 2^12 QTT decomposition, 1 launch per step"},
+}
 
 
 def _peaks():
@@ -324,7 +330,8 @@ def _roofline(st, peaks):
     name, (kms, kwork, bound, peak) = max(classes.items(), key=lambda kv: kv[1][0])
     achieved = kwork / (kms / 1e3) / 1e12 if kms > 0 else 0.0
     out = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
-           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(name, {}).get("bytes"),
+           "traffic_source": NCU_TRAFFIC.get(name, {}).get("source"),
            "peak_source": (("bf16 dense, measured, sustained (MEASURED_PEAKS.json bf16_tflops_sustained: the kernel's "
                             "launches run throughout the step)") if bound == "tensor" else
                            "FP32 FFMA: 128 per clock per SM x 152 SMs x 2070 MHz (derived)" if peak == FP32_PEAK_TFLOPS
@@ -403,6 +410,8 @@ def _configs(args, F, dev, flush, stream, world):
                                    "err_bound": math.sqrt(max(st["err2"], 0.0) / st["norm2"]),
                                    "stages_ms": {k: st[k] for k in STAGE_KEYS},
                                    "routes": {k: st[k] for k in ROUTE_KEYS}}
+                    if prec == "fp64" and name.startswith("clustered"):
+                        entry["adjoint_recompute"] = _adjoint_on(F, tt, idx, w, stream)
                     tt.free()
                 except Exception as e:
                     entry[prec] = {"error": str(e)[:300]}
@@ -414,6 +423,36 @@ def _configs(args, F, dev, flush, stream, world):
             entry["error"] = str(e)[:300]
         out[name] = entry
     return out
+
+
+def _adjoint_on(F, tt, idx, w, stream):
+    """Evaluation and adjoint (recomputed left partials, checkpointed every ceil(sqrt(d))
+    modes) of the decomposition's TT, cast to FP32, on all of the workload's entries with
+    upstream weights = the residuals a - v."""
+    import numpy as np
+    import torch
+    try:
+        cores = [c.float().contiguous() for c in tt.cores()]
+        vals = torch.from_numpy(np.asarray(w.vals, dtype=np.float32)).to(idx.device)
+        F.tt_eval_at(cores, idx)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        a = F.tt_eval_at(cores, idx)
+        e[1].record(stream)
+        grads = F.tt_eval_backward(cores, idx, a - vals, recompute=True)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        rk = tt.ranks
+        flops = w.nnz * 2.0 * 3.0 * sum(rk[k] * rk[k + 1] for k in range(len(rk) - 1))
+        out = {"entries": w.nnz, "ranks": rk, "dtype": "f32 cores", "eval_ms": fwd, "backward_ms": bwd,
+               "backward_tflops": flops / (bwd / 1e3) / 1e12,
+               "backward_fp32_frac": flops / (bwd / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+               "grad_norm": float(sum(float(g.double().norm()) ** 2 for g in grads) ** 0.5)}
+        del cores, grads, a
+        return out
+    except Exception as e:   # reported, never hidden
+        return {"error": str(e)[:300]}
 
 
 def _adjoint(args, F, dev, stream):
@@ -450,9 +489,14 @@ def _adjoint(args, F, dev, stream):
         # algorithmic HBM bytes: indices (8 x 4 B) + upstream gradient (4 B) per entry, cores L2-resident
         bytes_bwd = m * (8 * 4 + 4)
         flops_bwd = m * (2 * 2 * sum(ranks[k] * ranks[k + 1] for k in range(8)) + 2 * sum(ranks[k] * ranks[k + 1] for k in range(8)))
+        # the binding roof: ranks >= 16 take the index-sorted GEMM path (FP32 FFMA bound);
+        # the algorithmic flops are those of the two partial sweeps and the gradient
+        flops_sorted = m * 2.0 * 3.0 * sum(ranks[k] * ranks[k + 1] for k in range(8))
         out[f"rank{r}"] = {"eval_ms": fwd, "backward_ms": bwd, "backward_gbs": bytes_bwd / (bwd / 1e3) / 1e9,
                            "backward_hbm_frac": bytes_bwd / (bwd / 1e3) / 1e9 / hbm,
-                           "backward_tflops": flops_bwd / (bwd / 1e3) / 1e12}
+                           "backward_tflops": flops_bwd / (bwd / 1e3) / 1e12,
+                           "backward_fp32_frac": flops_sorted / (bwd / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                           "path": "index-sorted GEMM tiles" if r >= 16 else "one thread/warp per entry"}
         if r == 8:   # the fitting runs after every other measurement (see run_ours)
             out["_fit_args"] = (cores, idx, w, m)
     return out
@@ -611,6 +655,49 @@ def _e2e(args, w, F, dev, barrier, world):
             "h2d_bytes_per_step": int(w.idx.nbytes + w.vals.nbytes), "d2h_bytes_per_step": int(d2h)}
 
 
+PROFILE_CASES = ("grouping-qtt18", "adjoint-zipf1e6-r64", "decompose-qtt12", "decompose-qtt12-mixed",
+                 "decompose-uniform5")
+
+
+def run_profile_case(case):
+    """One call of one case, for profiler captures (no timing loop, no other lines):
+    grouping-qtt18: the banded 2^18 QTT (2.6e6 nonzeros) through value Depar (S1-S6);
+    adjoint-zipf1e6-r64: evaluation + adjoint of a rank-64 FP32 TT on 1e6 Zipf(1.2) entries
+    of the 100^8 tensor; decompose-qtt12[-mixed]: the headline decomposition once;
+    decompose-uniform5: the 50^5, 1e5-nonzero decomposition once."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1908_02721_gb300 import fasttt as F
+    from paper_1908_02721_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    if case == "adjoint-zipf1e6-r64":
+        w = W.zipf_tt(nnz=1_000_000)
+        idx = torch.from_numpy(w.idx).cuda()
+        rng = np.random.Generator(np.random.Philox(key=464))
+        ranks = [1] + [64] * 7 + [1]
+        cores = [torch.from_numpy((rng.standard_normal((ranks[k], 100, ranks[k + 1])) / math.sqrt(ranks[k]))
+                                  .astype(np.float32)).cuda() for k in range(8)]
+        g = torch.from_numpy(rng.standard_normal(w.nnz).astype(np.float32)).cuda()
+        a = F.tt_eval_at(cores, idx)
+        F.tt_eval_backward(cores, idx, g)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": case, "checksum": float(a.abs().sum())}))
+        return
+    if case == "grouping-qtt18":
+        w, kw = W.banded_qtt(18), {"stage": "depar", "keep_intermediates": True}
+    elif case == "decompose-uniform5":
+        w, kw = W.uniform5(seed=2), {}
+    else:
+        w, kw = W.banded_qtt(HEADLINE_M), {"precision": "mixed" if case.endswith("mixed") else "fp64"}
+    idx = torch.from_numpy(w.idx).cuda()
+    vals = torch.from_numpy(w.vals).cuda()
+    tt = F.fasttt_decompose(idx, vals, w.dims, w.eps, **kw)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "ranks": tt.ranks, "ms_total": tt.stats["ms_total"]}))
+    tt.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -626,7 +713,12 @@ def main():
     ap.add_argument("--no-config5", action="store_true", help="skip the 5e7-nonzero configuration")
     ap.add_argument("--workload", default="qtt12", choices=["qtt12", "qtt10"],
                     help="qtt10: the same recipe at 2^10 x 2^10, for profiler captures only")
+    ap.add_argument("--profile-case", choices=PROFILE_CASES,
+                    help="run one case once for a profiler capture and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
