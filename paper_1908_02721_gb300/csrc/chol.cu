@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kTrsmCols) trsm_leaf_kernel(const double* R, i
   double(*L)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(tsm);            // L = R^T, identity-padded
   double(*T)[kTrsmCols + 1] = reinterpret_cast<double(*)[kTrsmCols + 1]>(tsm + NB * (NB + 1));
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, j = e % NB;
+    const int j = e / NB, i = e % NB;   // consecutive threads read along row j of R
     double v;
     if (i < nb && j < nb) v = (j <= i) ? R[(int64_t)j * ldr + i] : 0.0;
     else v = (i == j) ? 1.0 : 0.0;

@@ -1265,14 +1265,15 @@ int64_t mixed_bonds_escalated() { return g_mixed_escalated.load(); }
 
 namespace {
 
-// Tall-skinny shapes wider than TSQR takes (lg >= 4n, n > kMaxTsqrCols): the tall
-// orientation T (A, column-major lg x n) = Q R by FP64 CholeskyQR2, one-sided Jacobi
-// on the n x n R only (R V = U_R Sigma), then A <- Q (R V) = T V by one FP64-level
-// GEMM: the same result as Jacobi on T (backward error u ||T||) with the sweeps on n
-// rows instead of lg.  False, A untouched, when the shape does not apply or
-// CholeskyQR2 breaks down (T too ill conditioned): the caller runs Jacobi on T.
+// Tall-skinny shapes (lg >= 4n, n >= 96; narrower ones are cheaper on TSQR): the tall
+// orientation T (A, column-major lg x n) = Q R by FP64 CholeskyQR2, one-sided Jacobi on
+// the n x n R only
+// (R V = U_R Sigma), then A <- Q (R V) = T V by one FP64-level GEMM: the same result
+// as Jacobi on T (backward error u ||T||) with the sweeps on n rows instead of lg.
+// False, A untouched, when the shape does not apply or CholeskyQR2 breaks down (T too
+// ill conditioned): the caller takes TSQR or Jacobi on T.
 bool cholqr_jacobi(double* A, int64_t lg, int n, double* V, int64_t max_sweeps, cudaStream_t s, int64_t& sweeps) {
-  if (n <= kMaxTsqrCols || lg < 4 * (int64_t)n) return false;
+  if (n < 96 || lg < 4 * (int64_t)n) return false;
   const int64_t nn = (int64_t)n * n;
   DBuf<double> Q((size_t)lg * n, s), R(nn, s), Rc(nn, s);
   FTT_CUDA(cudaMemcpyAsync(Q.get(), A, sizeof(double) * lg * n, cudaMemcpyDeviceToDevice, s));
@@ -1301,9 +1302,11 @@ void svd_direct(const double* Z, int64_t M, int64_t N,
   std::vector<double> h(n);
   identity_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(V.get(), n);
   FTT_LAUNCH();
-  if (tsqr_applies(lg, n)) {
+  if (cholqr_jacobi(A.get(), lg, n, V.get(), max_sweeps, s, out.sweeps)) {
+    // done: Jacobi on CholeskyQR2's R
+  } else if (tsqr_applies(lg, n)) {
     out.sweeps = tsqr_jacobi(A.get(), lg, n, V.get(), max_sweeps, s);
-  } else if (!cholqr_jacobi(A.get(), lg, n, V.get(), max_sweeps, s, out.sweeps)) {
+  } else {
     out.sweeps = jacobi_f64(A.get(), lg, lg, n, V.get(), n, n, max_sweeps, s);
   }
   {
