@@ -29,6 +29,29 @@ __device__ __forceinline__ void block_sum3(T& a, T& b, T& c) {
   a = red[0][0]; b = red[1][0]; c = red[2][0];
 }
 
+// Block-wide sum of three values for NW warps, summed in warp order (deterministic).
+template <typename T, int NW>
+__device__ __forceinline__ void block_sum3n(T& a, T& b, T& c) {
+  __shared__ T red[3][NW];
+  __syncthreads();  // earlier readers of red are done
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T x = 0, y = 0, z = 0;
+    for (int w = 0; w < NW; ++w) { x += red[0][w]; y += red[1][w]; z += red[2][w]; }
+    red[0][0] = x; red[1][0] = y; red[2][0] = z;
+  }
+  __syncthreads();
+  a = red[0][0]; b = red[1][0]; c = red[2][0];
+}
+
 // Grid-wide barrier of a cooperative launch (all blocks co-resident).  bar[0]
 // counts arrivals, bar[1] is the generation, bar[2] an error flag, bar[3] the poll
 // bound (0: kBarrierSpins).  The wait is bounded: after that many polls the block

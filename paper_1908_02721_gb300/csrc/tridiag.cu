@@ -48,8 +48,16 @@ __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (
 // written once every block has formed its copy of row k (after the barrier).
 constexpr int kMaxSeg = 8;
 
+// NW warps per block (one block per SM).  FP32: 32 warps hide the shared-memory and
+// load latency of the column passes; FP64: the FP64 pipe is the limit and 8 warps keep
+// it as busy as more would.
 template <typename T>
-__global__ void __launch_bounds__(256)
+struct TridiagWarps { static constexpr int value = 8; };
+template <>
+struct TridiagWarps<float> { static constexpr int value = 32; };
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32)
     tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* part, unsigned* bar) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
   T* vs = reinterpret_cast<T*>(vs_raw);   // v_k
@@ -57,7 +65,7 @@ __global__ void __launch_bounds__(256)
   T* ws = vp + n;                         // w_{k-1} = p - (tau/2)(p.v) v
   T* rk = ws + n;                         // row k after column k-1's update
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * 8 + warp, W = (int64_t)gridDim.x * 8;
+  const int64_t gw = (int64_t)blockIdx.x * NW + warp, W = (int64_t)gridDim.x * NW;
   unsigned gen = 0;
   T tprev = 0;   // tau_{k-1}
   int64_t nseg_prev = 1;
@@ -73,7 +81,7 @@ __global__ void __launch_bounds__(256)
       ws[j] = acc;   // tau already applied
       pv = fma(acc, vp[j], pv);
     }
-    block_sum3<T>(pv, z1, z2);   // ends with a barrier
+    block_sum3n<T, NW>(pv, z1, z2);   // ends with a barrier
     const T K = T(0.5) * tprev * pv;
     for (int64_t j = threadIdx.x; j < mp; j += blockDim.x) ws[j] = ws[j] - K * vp[j];
     __syncthreads();
@@ -96,7 +104,7 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     T s = 0, z1 = 0, z2 = 0;
     for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) s = fma(rk[j], rk[j], s);
-    block_sum3<T>(s, z1, z2);   // ends with a barrier
+    block_sum3n<T, NW>(s, z1, z2);   // ends with a barrier
     const T alpha = rk[0];
     T beta = alpha, tk = 0, scale = 0;
     if (s > T(0)) {
@@ -567,10 +575,12 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   // 1. tridiagonalisation
   {
     // the route's whole budget (not this call's need), so that concurrent callers never lower it
-    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<double, TridiagWarps<double>::value>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_max - 4096));
     int per = 0;
-    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<double>, 256, smem));
+    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<double, TridiagWarps<double>::value>,
+                                                           32 * TridiagWarps<double>::value, smem));
     const int grid = std::min(2, per) * sms;
     if (grid < 1) return false;
     DBuf<unsigned> bar(4, s);
@@ -583,7 +593,8 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
     KClock clk;
     kclock_begin(clk, KC_TRIDIAG, s);
     const cudaError_t err =
-        cudaLaunchCooperativeKernel((void*)tridiag_kernel<double>, dim3(grid), dim3(256), args, smem, s);
+        cudaLaunchCooperativeKernel((void*)tridiag_kernel<double, TridiagWarps<double>::value>, dim3(grid),
+                                    dim3(32 * TridiagWarps<double>::value), args, smem, s);
     if (err != cudaSuccess) {
       cudaGetLastError();
       return false;
@@ -714,10 +725,12 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   // 1. FP32 tridiagonalisation
   {
     // the route's whole budget (not this call's need), so that concurrent callers never lower it
-    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<float, TridiagWarps<float>::value>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_max - 4096));
     int per = 0;
-    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<float>, 256, smem));
+    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<float, TridiagWarps<float>::value>,
+                                                           32 * TridiagWarps<float>::value, smem));
     const int grid = std::min(2, per) * sms;
     if (grid < 1) return false;
     DBuf<unsigned> bar(4, s);
@@ -730,7 +743,8 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     KClock clk;
     kclock_begin(clk, KC_TRIDIAG32, s);
     const cudaError_t err =
-        cudaLaunchCooperativeKernel((void*)tridiag_kernel<float>, dim3(grid), dim3(256), args, smem, s);
+        cudaLaunchCooperativeKernel((void*)tridiag_kernel<float, TridiagWarps<float>::value>, dim3(grid),
+                                    dim3(32 * TridiagWarps<float>::value), args, smem, s);
     if (err != cudaSuccess) {
       cudaGetLastError();
       return false;
