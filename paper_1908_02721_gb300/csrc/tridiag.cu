@@ -60,10 +60,10 @@ template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32)
     tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* part, unsigned* bar) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
-  T* vs = reinterpret_cast<T*>(vs_raw);   // v_k
+  T* vs = reinterpret_cast<T*>(vs_raw);   // v_k, formed in place from rk
   T* vp = vs + n;                         // v_{k-1}
   T* ws = vp + n;                         // w_{k-1} = p - (tau/2)(p.v) v
-  T* rk = ws + n;                         // row k after column k-1's update
+  T* rk = vs;                             // row k after column k-1's update (v_k's buffer)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * NW + warp, W = (int64_t)gridDim.x * NW;
   unsigned gen = 0;
@@ -102,10 +102,11 @@ __global__ void __launch_bounds__(NW * 32)
       rk[j] = x;
     }
     __syncthreads();
+    // rk[0] is read before block_sum3n's barriers, so v_k below may overwrite it in place
+    const T alpha = rk[0];
     T s = 0, z1 = 0, z2 = 0;
     for (int64_t j = 1 + threadIdx.x; j < m; j += blockDim.x) s = fma(rk[j], rk[j], s);
     block_sum3n<T, NW>(s, z1, z2);   // ends with a barrier
-    const T alpha = rk[0];
     T beta = alpha, tk = 0, scale = 0;
     if (s > T(0)) {
       beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
@@ -161,8 +162,9 @@ __global__ void __launch_bounds__(NW * 32)
       if (lane == 0) part[(k & 1) * kMaxSeg * n + sg * n + i] = tk * acc;
     }
     if (!grid_barrier(bar, gridDim.x, gen)) return;
-    // v_k becomes the previous reflector
+    // v_k becomes the previous reflector; the old v_{k-1} buffer takes the next row
     T* t = vp; vp = vs; vs = t;
+    rk = vs;
     tprev = tk;
     nseg_prev = nseg;
   }
@@ -567,7 +569,7 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = 4 * sizeof(double) * (size_t)n;
+  const size_t smem = 3 * sizeof(double) * (size_t)n;
   if (!coop || smem + 4096 > (size_t)smem_max) return false;
   const int64_t nn = (int64_t)n * n;
   DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)2 * kMaxSeg * n, s);
@@ -695,7 +697,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = 4 * sizeof(float) * (size_t)n;
+  const size_t smem = 3 * sizeof(float) * (size_t)n;
   const int64_t nn = (int64_t)n * n;
   // every vector's tridiagonal factors are kept for the cluster iterations: 17 n^2 bytes
   if (!coop || smem + 4096 > (size_t)smem_max || 17.0 * (double)nn > 6.0e9) return false;
