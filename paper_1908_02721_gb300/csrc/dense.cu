@@ -1223,9 +1223,17 @@ struct EigStart {
 // the fast route, then the FP64 tridiagonal route, then the iterative one.
 bool gram_eig(const double* G, int n, double* V, std::vector<double>& h, int64_t max_sweeps, cudaStream_t s,
               bool mixed, EigStart& st0, int64_t& sweeps,
-              const std::function<bool(const std::vector<double>&)>& start_ok = nullptr) {
+              const std::function<bool(const std::vector<double>&)>& start_ok = nullptr,
+              const std::function<int64_t(const std::vector<double>&)>& topk = nullptr) {
   sweeps = 0;
   const int64_t nn = (int64_t)n * n;
+  // few eigenvectors wanted (a rank cap): the FP64 tridiagonal route computes only those
+  if (!mixed && topk) {
+    if (sym_eig_tridiag(G, n, V, h, s, false, topk)) {
+      note_eig(true);
+      return true;
+    }
+  }
   if (mixed) {
     if (!sym_eig_start_f32(G, n, V, h, s)) {
       st0.declined = true;
@@ -1489,16 +1497,27 @@ void sym_eig_iterative(const double* G, int n, double* V, std::vector<double>& l
 
 void svd_from_gram(const double* Gram, int64_t M, int64_t N,
                    const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
-                   SvdOut& out, cudaStream_t s, bool mixed) {
+                   SvdOut& out, cudaStream_t s, bool mixed, int64_t kcap) {
   if (M > INT32_MAX / 2) fail(FASTTT_ERANK, "SVD too large");
   const int n = (int)M;
   const int nsv = (int)std::min<int64_t>(n, N);
+  // the eigenvectors the rank rule will keep, plus a margin for ties at the boundary
+  auto topk = [&](const std::vector<double>& lam) -> int64_t {
+    std::vector<double> sg;
+    std::vector<int32_t> pm;
+    sigma_from_lambda(lam, sg, pm);
+    sg.resize(nsv);
+    const int64_t r = std::max<int64_t>(1, std::min<int64_t>(choose_rank(sg), nsv));
+    return std::min<int64_t>(n, r + 8);
+  };
+  const bool capped = kcap > 0 && 4 * kcap <= n;
   DBuf<double> V((size_t)n * n, s);
   std::vector<double> h(n);
   std::vector<int32_t> perm;
   EigStart st0;
   bool done = false;
-  if (mixed) {
+  if (mixed && capped) g_mixed_escalated.fetch_add(1);   // the top-k FP64 route is cheaper than any start
+  if (mixed && !capped) {
     // The Gram is an FP64 sum here: the error floor is the FP32-level refinement's
     int64_t sw = 0;
     auto start_ok = [&](const std::vector<double>& lam) {
@@ -1522,7 +1541,8 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
   }
   if (!done) {
     int64_t sw = 0;
-    gram_eig(Gram, n, V.get(), h, max_sweeps, s, false, st0, sw);
+    gram_eig(Gram, n, V.get(), h, max_sweeps, s, false, st0, sw, nullptr,
+             capped ? std::function<int64_t(const std::vector<double>&)>(topk) : nullptr);
     out.sweeps = sw;
     sigma_from_lambda(h, out.sigma_all, perm);
     out.sigma_all.resize(nsv);

@@ -102,7 +102,11 @@ void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<in
 // receives eigenvector j in V[j*n .. j*n + n), lam_out the eigenvalues.  mixed:
 // the back-transformation GEMMs run split-TF32.  Returns false (V undefined)
 // when the route does not apply or its vectors could not be made orthonormal.
-bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed);
+// need (optional): called with the eigenvalues (ascending) before any eigenvector is
+// formed, returns how many of the largest are wanted; only their vectors are computed
+// (the other rows of V are zero).
+bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed,
+                     const std::function<int64_t(const std::vector<double>&)>& need = nullptr);
 
 // The FP32 start of the fast eigensolver (tridiag.cu): G scaled by a power of
 // two and rounded to FP32, FP32 Householder tridiagonalisation, bisection and
@@ -129,9 +133,11 @@ void sym_eig_iterative(const double* G, int n, double* V, std::vector<double>& l
 // the min(M, N) singular values sqrt(max(lambda, 0)) descending (the other
 // eigenvalues are zero), r = choose_rank of those.
 // Fills out.r, out.sigma_all, out.sigma and out.U (M x r); out.Vt stays empty.
+// kcap > 0: no rank above kcap will be kept (a rank cap); when it is at most a quarter of
+// M, the FP64 tridiagonal route with only the kept eigenvectors goes first.
 void svd_from_gram(const double* Gram, int64_t M, int64_t N,
                    const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
-                   SvdOut& out, cudaStream_t s, bool mixed = false);
+                   SvdOut& out, cudaStream_t s, bool mixed = false, int64_t kcap = 0);
 
 // ---------------------------------------------------------------- chol.cu
 

@@ -56,14 +56,16 @@ struct TridiagWarps { static constexpr int value = 8; };
 template <>
 struct TridiagWarps<float> { static constexpr int value = 32; };
 
-template <typename T, int NW>
+// SHARED: the row and the reflector share one buffer (v_k formed in place), so that
+// three vectors of n values fit where four would not (n above ~7,000 in FP64).
+template <typename T, int NW, bool SHARED>
 __global__ void __launch_bounds__(NW * 32)
     tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* part, unsigned* bar) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
-  T* vs = reinterpret_cast<T*>(vs_raw);   // v_k, formed in place from rk
+  T* vs = reinterpret_cast<T*>(vs_raw);   // v_k
   T* vp = vs + n;                         // v_{k-1}
   T* ws = vp + n;                         // w_{k-1} = p - (tau/2)(p.v) v
-  T* rk = vs;                             // row k after column k-1's update (v_k's buffer)
+  T* rk = SHARED ? vs : ws + n;           // row k after column k-1's update
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * NW + warp, W = (int64_t)gridDim.x * NW;
   unsigned gen = 0;
@@ -162,9 +164,9 @@ __global__ void __launch_bounds__(NW * 32)
       if (lane == 0) part[(k & 1) * kMaxSeg * n + sg * n + i] = tk * acc;
     }
     if (!grid_barrier(bar, gridDim.x, gen)) return;
-    // v_k becomes the previous reflector; the old v_{k-1} buffer takes the next row
+    // v_k becomes the previous reflector (SHARED: the old v_{k-1} buffer takes the next row)
     T* t = vp; vp = vs; vs = t;
-    rk = vs;
+    if (SHARED) rk = vs;
     tprev = tk;
     nseg_prev = nseg;
   }
@@ -318,7 +320,7 @@ __device__ void normalise_col(int64_t n, T* z, int64_t ldz) {
 template <typename T>
 __global__ void inverse_iteration_kernel(const T* d, const T* e, int64_t n, const T* shift, int64_t j0, int64_t nv,
                                          T pert, T* sdd, T* sdu, T* sdu2, T* sdl, unsigned char* spiv, T* Z,
-                                         int64_t ldz) {
+                                         int64_t ldz, int64_t zc0) {
   constexpr int kInvIters = 3;   // fewer leave the refinement's start too rough (more Rayleigh-Ritz work)
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nv) return;
@@ -357,7 +359,7 @@ __global__ void inverse_iteration_kernel(const T* d, const T* e, int64_t n, cons
     if (fabs(piv) < pert) piv = copysign(pert, piv);
     S(sdd, i) = T(1) / piv;   // the solves multiply by the reciprocal pivots
   }
-  T* z = Z + j;
+  T* z = Z + (j - zc0);   // vector j in column j - zc0 of Z
   for (int64_t i = 0; i < n; ++i) z[i * ldz] = (T)start_component(i, j);
   for (int it = 0; it < kInvIters; ++it) {
     tri_solve<T>(n, nv, t, sdd, sdu, sdu2, sdl, spiv, z, ldz);
@@ -513,11 +515,14 @@ double frob2(const double* R, int64_t count, cudaStream_t s) {
 // k+1 on, v_0 = 1; tau on the device), blocks of kWYBlock reflectors from the
 // last to the first in the compact WY form I - V T V^T.  mixed: the two large
 // products of each block at FP32 level.
-void wy_back_transform(const double* A, const double* tau, int64_t n, double* Z, bool mixed, cudaStream_t s) {
+void wy_back_transform(const double* A, const double* tau, int64_t n, double* Z, bool mixed, cudaStream_t s,
+                       int64_t nz = 0) {
+  // Z: n rows x nz columns (row-major, leading dimension nz)
+  if (nz <= 0) nz = n;
   const int64_t nrefl = n - 2;
   if (nrefl < 1) return;
   DBuf<double> Vb((size_t)(n - 1) * kWYBlock, s), S((size_t)kWYBlock * kWYBlock, s),
-      T((size_t)kWYBlock * kWYBlock, s), W1((size_t)kWYBlock * n, s), W2((size_t)kWYBlock * n, s);
+      T((size_t)kWYBlock * kWYBlock, s), W1((size_t)kWYBlock * nz, s), W2((size_t)kWYBlock * nz, s);
   for (int64_t k0 = ((nrefl - 1) / kWYBlock) * kWYBlock; k0 >= 0; k0 -= kWYBlock) {
     const int64_t kb = std::min<int64_t>(kWYBlock, nrefl - k0), nr = n - k0 - 1;
     wy_vectors_kernel<<<grid_for(nr * kb), 256, 0, s>>>(A, n, k0, kb, Vb.get());
@@ -528,10 +533,10 @@ void wy_back_transform(const double* A, const double* tau, int64_t n, double* Z,
     FTT_LAUNCH();
     wy_t_kernel<<<1, 256, 0, s>>>(S.get(), tau + k0, kb, T.get());
     FTT_LAUNCH();
-    double* Zs = Z + (k0 + 1) * n;
-    gemm(mixed, kb, n, nr, 1.0, Vb.get(), 1, kb, Zs, n, 1, 0.0, W1.get(), n, 1, s);   // V^T Z
-    gemm_f64(kb, n, kb, 1.0, T.get(), kb, 1, W1.get(), n, 1, 0.0, W2.get(), n, 1, s);  // T (V^T Z)
-    gemm(mixed, nr, n, kb, -1.0, Vb.get(), kb, 1, W2.get(), n, 1, 1.0, Zs, n, 1, s);  // Z -= V T V^T Z
+    double* Zs = Z + (k0 + 1) * nz;
+    gemm(mixed, kb, nz, nr, 1.0, Vb.get(), 1, kb, Zs, nz, 1, 0.0, W1.get(), nz, 1, s);   // V^T Z
+    gemm_f64(kb, nz, kb, 1.0, T.get(), kb, 1, W1.get(), nz, 1, 0.0, W2.get(), nz, 1, s);  // T (V^T Z)
+    gemm(mixed, nr, nz, kb, -1.0, Vb.get(), kb, 1, W2.get(), nz, 1, 1.0, Zs, nz, 1, s);  // Z -= V T V^T Z
   }
 }
 
@@ -562,27 +567,29 @@ __global__ void identity64_kernel(double* V, int64_t n) {
 
 }  // namespace
 
-bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed) {
+bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed,
+                     const std::function<int64_t(const std::vector<double>&)>& need) {
   if (n < 3) return false;
   int dev = 0, coop = 0, sms = 0, smem_max = 0;
   FTT_CUDA(cudaGetDevice(&dev));
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = 3 * sizeof(double) * (size_t)n;
+  // four vectors of n values in shared memory when they fit, three (row and reflector shared) otherwise
+  const bool shared_rk = 4 * sizeof(double) * (size_t)n + 4096 > (size_t)smem_max;
+  const size_t smem = (shared_rk ? 3 : 4) * sizeof(double) * (size_t)n;
   if (!coop || smem + 4096 > (size_t)smem_max) return false;
   const int64_t nn = (int64_t)n * n;
   DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)2 * kMaxSeg * n, s);
   FTT_CUDA(cudaMemcpyAsync(A.get(), G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   // 1. tridiagonalisation
   {
+    constexpr int NW = TridiagWarps<double>::value;
+    void* fn = shared_rk ? (void*)tridiag_kernel<double, NW, true> : (void*)tridiag_kernel<double, NW, false>;
     // the route's whole budget (not this call's need), so that concurrent callers never lower it
-    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<double, TridiagWarps<double>::value>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  smem_max - 4096));
+    FTT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max - 4096));
     int per = 0;
-    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<double, TridiagWarps<double>::value>,
-                                                           32 * TridiagWarps<double>::value, smem));
+    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * NW, smem));
     const int grid = std::min(2, per) * sms;
     if (grid < 1) return false;
     DBuf<unsigned> bar(4, s);
@@ -594,9 +601,7 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
     void* args[] = {(void*)&Ap, (void*)&n64, (void*)&dp, (void*)&ep, (void*)&tp, (void*)&pp, (void*)&bp};
     KClock clk;
     kclock_begin(clk, KC_TRIDIAG, s);
-    const cudaError_t err =
-        cudaLaunchCooperativeKernel((void*)tridiag_kernel<double, TridiagWarps<double>::value>, dim3(grid),
-                                    dim3(32 * TridiagWarps<double>::value), args, smem, s);
+    const cudaError_t err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(32 * NW), args, smem, s);
     if (err != cudaSuccess) {
       cudaGetLastError();
       return false;
@@ -643,48 +648,54 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   std::vector<double> hl(n);
   FTT_CUDA(cudaMemcpyAsync(hl.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   FTT_CUDA(cudaStreamSynchronize(s));
+  // eigenvectors wanted: the kv largest (all unless the caller needs fewer)
+  const int64_t kv = need ? std::max<int64_t>(1, std::min<int64_t>(n, need(hl))) : n;
+  const int64_t v0 = n - kv;   // eigenvalues ascending: vectors v0 .. n-1
   // shifts for inverse iteration: eigenvalues closer than sep are moved apart
   const double sep = 16.0 * 0x1p-53 * tnorm;
   std::vector<double> hs(hl);
   for (int i = 1; i < n; ++i)
     if (hs[i] - hs[i - 1] < sep) hs[i] = hs[i - 1] + sep;
   FTT_CUDA(cudaMemcpyAsync(shift.get(), hs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  // 3. eigenvectors of T, in batches bounding the scratch to ~2 GB
-  DBuf<double> Z(nn, s);
+  // 3. eigenvectors of T (Z: n x kv, column c = vector v0 + c), in batches bounding the scratch
+  const int64_t nk = (int64_t)n * kv;
+  DBuf<double> Z(nk, s);
   {
-    const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(2.0e9 / (33.0 * n))));
+    const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(kv, (int64_t)(2.0e9 / (33.0 * n))));
     DBuf<double> sdd(n * batch, s), sdu(n * batch, s), sdu2(n * batch, s), sdl(n * batch, s);
     DBuf<unsigned char> spiv(n * batch, s);
     const double pert = 0x1p-53 * std::max(tnorm, 1e-300);
-    for (int64_t j0 = 0; j0 < n; j0 += batch) {
+    for (int64_t j0 = v0; j0 < n; j0 += batch) {
       const int64_t nv = std::min<int64_t>(batch, n - j0);
       inverse_iteration_kernel<<<(unsigned)ceil_div(nv, 32), 32, 0, s>>>(
           d.get(), e.get(), n, shift.get(), j0, nv, pert, sdd.get(), sdu.get(), sdu2.get(), sdl.get(), spiv.get(),
-          Z.get(), n);
+          Z.get(), kv, v0);
       FTT_LAUNCH();
     }
   }
   kclock_end(clk2, 0.0, s);
-  // 4. orthonormalise Z (rows of T's basis, columns = vectors) in FP64
+  // 4. orthonormalise Z's columns in FP64
   {
-    DBuf<double> R(nn, s), Z0(nn, s);
+    const int64_t kk = kv * kv;
+    DBuf<double> R(kk, s), Z0(nk, s);
     bool ok = false;
     for (int it = 0; it < 4; ++it) {
-      gemm_f64(n, n, n, 1.0, Z.get(), 1, n, Z.get(), n, 1, 0.0, R.get(), n, 1, s, true);   // Z^T Z
-      i_minus_sym_kernel<<<grid_for(nn), 256, 0, s>>>(R.get(), n);
+      gemm_f64(kv, kv, n, 1.0, Z.get(), 1, kv, Z.get(), kv, 1, 0.0, R.get(), kv, 1, s, true);   // Z^T Z
+      i_minus_sym_kernel<<<grid_for(kk), 256, 0, s>>>(R.get(), kv);
       FTT_LAUNCH();
-      const double rF = sqrt(frob2(R.get(), nn, s));
+      const double rF = sqrt(frob2(R.get(), kk, s));
       if (!(rF < 0.5)) break;
       if (rF <= 16.0 * (double)n * 0x1p-53) { ok = true; break; }
-      FTT_CUDA(cudaMemcpyAsync(Z0.get(), Z.get(), sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-      gemm_f64(n, n, n, 0.5, Z0.get(), n, 1, R.get(), n, 1, 1.0, Z.get(), n, 1, s);   // Z += Z R / 2
+      FTT_CUDA(cudaMemcpyAsync(Z0.get(), Z.get(), sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
+      gemm_f64(n, kv, kv, 0.5, Z0.get(), kv, 1, R.get(), kv, 1, 1.0, Z.get(), kv, 1, s);   // Z += Z R / 2
       ok = (it == 3);
     }
     if (!ok) return false;
   }
-  // 5. X = Q Z
-  wy_back_transform(A.get(), tau.get(), n, Z.get(), mixed, s);
-  transpose_f64(Z.get(), n, n, V, s);   // V: column j = eigenvector j
+  // 5. X = Q Z; V row j = eigenvector j (rows of the vectors not computed are zero)
+  wy_back_transform(A.get(), tau.get(), n, Z.get(), mixed, s, kv);
+  if (kv < n) FTT_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * n * v0, s));
+  transpose_f64(Z.get(), n, kv, V + v0 * n, s);
   lam_out = hl;
   return true;
 }
@@ -697,7 +708,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = 3 * sizeof(float) * (size_t)n;
+  const size_t smem = 4 * sizeof(float) * (size_t)n;
   const int64_t nn = (int64_t)n * n;
   // every vector's tridiagonal factors are kept for the cluster iterations: 17 n^2 bytes
   if (!coop || smem + 4096 > (size_t)smem_max || 17.0 * (double)nn > 6.0e9) return false;
@@ -727,11 +738,11 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   // 1. FP32 tridiagonalisation
   {
     // the route's whole budget (not this call's need), so that concurrent callers never lower it
-    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<float, TridiagWarps<float>::value>,
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_kernel<float, TridiagWarps<float>::value, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_max - 4096));
     int per = 0;
-    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<float, TridiagWarps<float>::value>,
+    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_kernel<float, TridiagWarps<float>::value, false>,
                                                            32 * TridiagWarps<float>::value, smem));
     const int grid = std::min(2, per) * sms;
     if (grid < 1) return false;
@@ -745,7 +756,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     KClock clk;
     kclock_begin(clk, KC_TRIDIAG32, s);
     const cudaError_t err =
-        cudaLaunchCooperativeKernel((void*)tridiag_kernel<float, TridiagWarps<float>::value>, dim3(grid),
+        cudaLaunchCooperativeKernel((void*)tridiag_kernel<float, TridiagWarps<float>::value, false>, dim3(grid),
                                     dim3(32 * TridiagWarps<float>::value), args, smem, s);
     if (err != cudaSuccess) {
       cudaGetLastError();
@@ -820,7 +831,7 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     const float pert = (float)(u32 * tnorm);
     inverse_iteration_kernel<float><<<(unsigned)ceil_div(n, 32), 32, 0, s>>>(
         d.get(), e.get(), n, shift.get(), 0, n, pert, sdd.get(), sdu.get(), sdu2.get(), sdl.get(), spiv.get(),
-        Z.get(), n);
+        Z.get(), n, 0);
     FTT_LAUNCH();
     if (!cb.empty()) {
       DBuf<int32_t> dcb(cb.size(), s);
