@@ -538,11 +538,11 @@ __global__ void to_f64_kernel(const float* a, int64_t n, double* b) { GRID_STRID
 __global__ void identity_f32_kernel(float* V, int64_t n) {
   GRID_STRIDE(i, n * n) V[i] = ((i / n) == (i % n)) ? 1.0f : 0.0f;
 }
-// C (n x n, row-major): lower triangle := upper triangle
-__global__ void mirror_upper_kernel(double* C, int64_t n) {
+// C (n x n, row-major, leading dimension ldc): lower triangle := upper triangle
+__global__ void mirror_upper_kernel(double* C, int64_t n, int64_t ldc) {
   GRID_STRIDE(e, n * n) {
     const int64_t i = e / n, j = e % n;
-    if (i > j) C[e] = C[j * n + i];
+    if (i > j) C[i * ldc + j] = C[j * ldc + i];
   }
 }
 // out (M x r) = U (M x r) with column c scaled by scale[c]
@@ -1137,7 +1137,7 @@ void gemm_f64_dfma(int64_t M, int64_t N, int64_t K, double alpha, const double* 
                    const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
                    cudaStream_t s, bool sym) {
   if (M <= 0 || N <= 0) return;
-  if (sym && (M != N || sci != N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
+  if (sym && (M != N || sci < N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
   const int64_t gx = ceil_div(M, kTile), gy = ceil_div(N, kTile);
   if (gy > 65535) fail(FASTTT_ERANK, "GEMM: N too large");
   dim3 grid((unsigned)gx, (unsigned)gy);
@@ -1148,7 +1148,7 @@ void gemm_f64_dfma(int64_t M, int64_t N, int64_t K, double alpha, const double* 
   // algorithmic flops: the full product (a symmetric product's mirrored half is not counted twice)
   kclock_end(clk, (sym ? 1.0 : 2.0) * (double)M * (double)N * (double)K + (sym ? (double)M * K : 0.0), s);
   if (sym) {
-    mirror_upper_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M);
+    mirror_upper_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M, sci);
     FTT_LAUNCH();
   }
 }

@@ -9,7 +9,8 @@
 namespace fasttt {
 
 // C(i,j) = alpha * sum_k A(i,k) B(k,j) + beta * C(i,j) with element strides, to
-// FP64 accuracy.  sym = true: C is known to be symmetric (square, row-major);
+// FP64 accuracy.  sym = true: C is known to be symmetric (square, row-major, scj = 1,
+// leading dimension sci >= N);
 // only tiles on or above the diagonal are computed and the lower triangle is
 // mirrored.  A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj],
 // C(i,j) = C[i*sci + j*scj].  Large products run on the tensor cores (exact bf16

@@ -505,10 +505,10 @@ void oz_split(const double* X, int64_t rows, int64_t cols, int64_t s_row, int64_
   FTT_LAUNCH();
 }
 
-__global__ void mirror_upper_oz_kernel(double* C, int64_t n) {
+__global__ void mirror_upper_oz_kernel(double* C, int64_t n, int64_t ldc) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / n, j = e % n;
-    if (i > j) C[e] = C[j * n + i];
+    if (i > j) C[i * ldc + j] = C[j * ldc + i];
   }
 }
 
@@ -543,7 +543,7 @@ bool run_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
   FTT_LAUNCH();
   kclock_end(clk, (sym ? 1.0 : 2.0) * (double)M * (double)N * (double)K, s);
   if (sym) {
-    mirror_upper_oz_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M);
+    mirror_upper_oz_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M, sci);
     FTT_LAUNCH();
   }
   return true;
@@ -584,7 +584,7 @@ bool gemm_ozaki(int slices, int64_t M, int64_t N, int64_t K, double alpha, const
                 const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
                 cudaStream_t s, bool sym) {
   if (M <= 0 || N <= 0) return true;
-  if (sym && (M != N || sci != N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
+  if (sym && (M != N || sci < N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
   if (K <= 0) return false;
   // FP64 level: 8 slices of 7 bits (level sums exact over windows of 384: 384 x 40960 < 2^24);
   // FP32 level: 3 slices of 8 bits (windows of 192: 192 x 81920 < 2^24)

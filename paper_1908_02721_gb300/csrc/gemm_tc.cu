@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(256)
       }
 }
 
-__global__ void mirror_upper_tc_kernel(double* C, int64_t n) {
+__global__ void mirror_upper_tc_kernel(double* C, int64_t n, int64_t ldc) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / n, j = e % n;
-    if (i > j) C[e] = C[j * n + i];
+    if (i > j) C[i * ldc + j] = C[j * ldc + i];
   }
 }
 
@@ -157,7 +157,7 @@ void gemm_tf32x3(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                  const double* B, int64_t sbk, int64_t sbj, double beta, double* C, int64_t sci, int64_t scj,
                  cudaStream_t s, bool sym) {
   if (M <= 0 || N <= 0) return;
-  if (sym && (M != N || sci != N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
+  if (sym && (M != N || sci < N || scj != 1)) fail(FASTTT_EINVAL, "symmetric GEMM needs a square row-major C");
   const int64_t gx = ceil_div(M, BM), gy = ceil_div(N, BN);
   if (gy > 65535) fail(FASTTT_ERANK, "GEMM: N too large");
   KClock clk;
@@ -167,7 +167,7 @@ void gemm_tf32x3(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
   FTT_LAUNCH();
   kclock_end(clk, (sym ? 1.0 : 2.0) * (double)M * (double)N * (double)K + (sym ? (double)M * K : 0.0), s);
   if (sym) {
-    mirror_upper_tc_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M);
+    mirror_upper_tc_kernel<<<grid_for(M * M), 256, 0, s>>>(C, M, sci);
     FTT_LAUNCH();
   }
 }

@@ -32,6 +32,8 @@ namespace {
 
 constexpr int kWYBlock = 64;
 constexpr int kClusterMax = 256;   // largest eigenvalue cluster of the FP32 start
+constexpr int kPanel = 64;         // columns per panel of the blocked FP64 tridiagonalisation
+constexpr int kPanelTail = 512;    // columns left to the unblocked kernel
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -60,12 +62,13 @@ struct TridiagWarps<float> { static constexpr int value = 32; };
 // three vectors of n values fit where four would not (n above ~7,000 in FP64).
 template <typename T, int NW, bool SHARED>
 __global__ void __launch_bounds__(NW * 32)
-    tridiag_kernel(T* A, int64_t n, T* d, T* e, T* tau, T* part, unsigned* bar) {
+    tridiag_kernel(T* A, int64_t n, int64_t k0, T* d, T* e, T* tau, T* part, unsigned* bar) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
+  const int64_t cap = n - k0;             // longest vector: the first column's trailing size + 1
   T* vs = reinterpret_cast<T*>(vs_raw);   // v_k
-  T* vp = vs + n;                         // v_{k-1}
-  T* ws = vp + n;                         // w_{k-1} = p - (tau/2)(p.v) v
-  T* rk = SHARED ? vs : ws + n;           // row k after column k-1's update
+  T* vp = vs + cap;                       // v_{k-1}
+  T* ws = vp + cap;                       // w_{k-1} = p - (tau/2)(p.v) v
+  T* rk = SHARED ? vs : ws + cap;         // row k after column k-1's update
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * NW + warp, W = (int64_t)gridDim.x * NW;
   unsigned gen = 0;
@@ -88,10 +91,12 @@ __global__ void __launch_bounds__(NW * 32)
     for (int64_t j = threadIdx.x; j < mp; j += blockDim.x) ws[j] = ws[j] - K * vp[j];
     __syncthreads();
   };
-  for (int64_t k = 0; k + 2 < n; ++k) {
+  // columns k0 .. n-3 (k0 > 0: the columns before were reduced by the blocked panels, whose
+  // updates the trailing matrix has taken in full)
+  for (int64_t k = k0; k + 2 < n; ++k) {
     const int64_t m = n - k - 1;
-    const bool upd = (k > 0) && (tprev != T(0));   // column k-1's update is not the identity
-    if (k > 0) {
+    const bool upd = (k > k0) && (tprev != T(0));   // column k-1's update is not the identity
+    if (k > k0) {
       form_w(m + 1, k - 1);
       // every block has read row k-1 (before the last barrier): keep v_{k-1} there now
       if (blockIdx.x == 0)
@@ -171,14 +176,14 @@ __global__ void __launch_bounds__(NW * 32)
     nseg_prev = nseg;
   }
   // the last 2 x 2 block after the last column's update; v of the last column into its row
-  if (n >= 3) {
+  if (n >= 3 && k0 + 2 < n) {
     form_w(2, n - 3);
     if (blockIdx.x == 0)
       for (int64_t j = threadIdx.x; j < 2; j += blockDim.x) A[(n - 3) * n + n - 2 + j] = vp[j];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (n >= 2) {
-      const bool upd = (n >= 3) && (tprev != T(0));
+      const bool upd = (n >= 3) && (k0 + 2 < n) && (tprev != T(0));
       T a00 = __ldcg(A + (n - 2) * n + n - 2), a01 = __ldcg(A + (n - 2) * n + n - 1),
         a11 = __ldcg(A + (n - 1) * n + n - 1);
       if (upd) {
@@ -193,6 +198,181 @@ __global__ void __launch_bounds__(NW * 32)
     } else {
       d[n - 1] = __ldcg(A + (n - 1) * n + n - 1);
     }
+  }
+}
+
+// Blocked Householder tridiagonalisation (Dongarra, Sorensen & Hammarling, "Block
+// reduction of matrices to condensed forms for eigenvalue computations", J. Comput.
+// Appl. Math. 27, 1989): one cooperative launch reduces a panel of nb columns
+// k0 .. k0+nb-1 without updating the trailing matrix A0.  With V = [v_0 .. v_{j-1}] and
+// W = [w_0 .. w_{j-1}] the panel's reflectors and update vectors so far, the current
+// matrix is A0 - V W^T - W V^T, so for column k = k0 + j
+//   p = tau (A0 v - V (W^T v) - W (V^T v)),   w = p - (tau/2)(p.v) v,
+// and row k+1 of the current matrix is A0's row minus the same sums.  The FP64 pipe does
+// the product A0 v (read only, one pass over the trailing matrix) and sums of length
+// 2j; the host then applies A0 -= V W^T + W V^T to the rows and columns after the panel
+// as one symmetric product of inner dimension 2 nb on the slice GEMM.
+//   X: 3 nb vectors of n values: V_t at t n, W_t at (nb + t) n, V_t again at (2 nb + t) n
+//      (so that [V W] and [W V] are both nb-strided operands of the product);
+//   part: kMaxSeg x (n + 2 nb) segment partials of A0 v (rows 0 .. m-1), V^T v (m ..) and
+//      W^T v (m + j ..); bpart: one partial of v.(A0 v) per block;
+//   rowbuf: row k+1 (columns k+2 ..) minus the panel's terms before column k, its
+//      diagonal at rowbuf[n].
+// Two grid barriers per column: after the products, and after w_k and row k+1's partial
+// sums are written.  Row k keeps v_k (v_0 = 1 stored) for the back-transformation, as in
+// tridiag_kernel.  gen0: the barrier generation at launch (the barrier words persist
+// across the panels' launches).
+template <int NW>
+__global__ void __launch_bounds__(NW * 32)
+    tridiag_panel_kernel(double* A, int64_t n, int64_t k0, int nb, double* d, double* e, double* tau, double* X,
+                         double* part, double* rowbuf, double* bpart, unsigned* bar, unsigned gen0) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double* vs = reinterpret_cast<double*>(sm_raw);   // row k, then v_k in place (n values)
+  double* yz = vs + n;                              // z_t = V_t.v (t < j), y_t = W_t.v at j + t
+  double* vw = yz + 2 * nb;                         // V_t[k+1] (t < nb), W_t[k+1] at nb + t
+  double* red = vw + 2 * nb;                        // NW x 32 partial sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * NW + warp, W = (int64_t)gridDim.x * NW;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, GT = (int64_t)gridDim.x * blockDim.x;
+  const int64_t ps = n + 2 * (int64_t)nb;
+  double* Vx = X;
+  double* Wx = X + (int64_t)nb * n;
+  double* V2 = X + 2 * (int64_t)nb * n;
+  unsigned gen = gen0;
+  for (int j = 0; j < nb; ++j) {
+    const int64_t k = k0 + j, m = n - k - 1;
+    // A. row k of the current matrix, then reflector k formed in place (every block)
+    double dk;
+    if (j == 0) {
+      for (int64_t c = threadIdx.x; c < m; c += blockDim.x) vs[c] = __ldcg(A + k * n + k + 1 + c);
+      dk = __ldcg(A + k * n + k);
+    } else {   // column k-1's term on top of rowbuf: V_{j-1}[k] = 1, W_{j-1}[k] = w_{k-1}[0]
+      const double* vq = Vx + (int64_t)(j - 1) * n;
+      const double* wq = Wx + (int64_t)(j - 1) * n;
+      const double a1 = __ldcg(vq + k), b1 = __ldcg(wq + k);
+      for (int64_t c = threadIdx.x; c < m; c += blockDim.x)
+        vs[c] = __ldcg(rowbuf + c) - a1 * __ldcg(wq + k + 1 + c) - b1 * __ldcg(vq + k + 1 + c);
+      dk = __ldcg(rowbuf + n) - 2.0 * a1 * b1;
+    }
+    __syncthreads();
+    const double alpha = vs[0];
+    double sq = 0, z1 = 0, z2 = 0;
+    for (int64_t c = 1 + threadIdx.x; c < m; c += blockDim.x) sq = fma(vs[c], vs[c], sq);
+    block_sum3n<double, NW>(sq, z1, z2);   // ends with a barrier
+    double beta = alpha, tk = 0, scale = 0;
+    if (sq > 0.0) {
+      beta = -copysign(sqrt(fma(alpha, alpha, sq)), alpha);
+      tk = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    for (int64_t c = threadIdx.x; c < m; c += blockDim.x) vs[c] = (c == 0) ? 1.0 : vs[c] * scale;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      d[k] = dk;
+      e[k] = beta;
+      tau[k] = tk;
+    }
+    // B. A0 v over rows k+1 .., then V_t.v and W_t.v (t < j): rows of length m, cut
+    //    into segments so that every warp has work; lane 0 keeps v.(A0 v) of its rows
+    const int64_t rows = m + 2 * (int64_t)j;
+    const int64_t nseg = max((int64_t)1, min((int64_t)kMaxSeg, W / rows));
+    const int64_t seg = ((m + nseg - 1) / nseg + 31) / 32 * 32;
+    double pv = 0;
+    for (int64_t task = gw; task < rows * nseg; task += W) {
+      const int64_t i = task / nseg, sg = task % nseg;
+      const double* row = i < m ? A + (k + 1 + i) * n + k + 1
+                                : (i - m < j ? Vx + (i - m) * n + k + 1 : Wx + (i - m - j) * n + k + 1);
+      const int64_t j0 = sg * seg, j1 = min(m, j0 + seg);
+      double a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = 0;
+      int64_t c = j0 + lane;
+      for (; c + 224 < j1; c += 256) {
+        double r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r[u] = __ldcg(row + c + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = fma(r[u], vs[c + 32 * u], a[u]);
+      }
+      for (; c < j1; c += 32) a[0] = fma(__ldcg(row + c), vs[c], a[0]);
+      double acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        part[sg * ps + i] = acc;
+        if (i < m) pv = fma(acc, vs[i], pv);
+      }
+    }
+    z1 = 0;
+    z2 = 0;
+    block_sum3n<double, NW>(pv, z1, z2);
+    if (threadIdx.x == 0) bpart[blockIdx.x] = pv;
+    if (!grid_barrier(bar, gridDim.x, gen)) return;
+    // C. z, y, v.(A0 v) (every block, fixed order); the panel's V_t[k+1], W_t[k+1]
+    if (threadIdx.x < 2 * j) {
+      double a = 0;
+      for (int64_t sg = 0; sg < nseg; ++sg) a += __ldcg(part + sg * ps + m + threadIdx.x);
+      yz[threadIdx.x] = a;
+    }
+    if (threadIdx.x < j) {
+      vw[threadIdx.x] = __ldcg(Vx + (int64_t)threadIdx.x * n + k + 1);
+      vw[nb + threadIdx.x] = __ldcg(Wx + (int64_t)threadIdx.x * n + k + 1);
+    }
+    double pvs = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) pvs += __ldcg(bpart + b);
+    z1 = 0;
+    z2 = 0;
+    block_sum3n<double, NW>(pvs, z1, z2);   // ends with a barrier: yz, vw visible
+    double yzs = 0;
+    for (int t = 0; t < j; ++t) yzs = fma(yz[t], yz[j + t], yzs);
+    // v.w = tau (v.A0 v - 2 y.z);  K = (tau / 2) v.w
+    const double K = 0.5 * tk * tk * (pvs - 2.0 * yzs);
+    // D. w_k = tau (A0 v - V y - W z) - K v into W, v_k into V, its copy and row k of A;
+    //    row k+1 (columns k+2 ..) less the terms of columns before k into rowbuf.  Tasks of
+    //    32 consecutive elements per block: warp q sums the terms t = q, q + NW, .. and the
+    //    block adds the NW partials in warp order.
+    const int64_t nw = (m + 31) / 32, nr = (j + 1 < nb) ? (m - 1 + 31) / 32 : 0;
+    for (int64_t task = blockIdx.x; task < nw + nr; task += gridDim.x) {
+      const bool isw = task < nw;
+      const int64_t g = (isw ? task : task - nw) * 32 + lane, len = isw ? m : m - 1;
+      double acc = 0;
+      if (g < len) {
+        if (isw) {
+#pragma unroll 4
+          for (int t = warp; t < j; t += NW)
+            acc += __ldcg(Vx + (int64_t)t * n + k + 1 + g) * yz[j + t] + __ldcg(Wx + (int64_t)t * n + k + 1 + g) * yz[t];
+        } else {
+#pragma unroll 4
+          for (int t = warp; t < j; t += NW)
+            acc += vw[t] * __ldcg(Wx + (int64_t)t * n + k + 2 + g) + vw[nb + t] * __ldcg(Vx + (int64_t)t * n + k + 2 + g);
+        }
+      }
+      red[warp * 32 + lane] = acc;
+      __syncthreads();
+      if (warp == 0 && g < len) {
+        double sacc = 0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) sacc += red[q * 32 + lane];
+        if (isw) {
+          double p = 0;
+          for (int64_t sg = 0; sg < nseg; ++sg) p += __ldcg(part + sg * ps + g);
+          const double vi = vs[g];
+          Wx[(int64_t)j * n + k + 1 + g] = tk * (p - sacc) - K * vi;
+          Vx[(int64_t)j * n + k + 1 + g] = vi;
+          V2[(int64_t)j * n + k + 1 + g] = vi;
+          A[k * n + k + 1 + g] = vi;
+        } else {
+          rowbuf[g] = __ldcg(A + (k + 1) * n + k + 2 + g) - sacc;
+        }
+      }
+      __syncthreads();
+    }
+    if (j + 1 < nb && gt == 0) {
+      double dd = __ldcg(A + (k + 1) * n + k + 1);
+      for (int t = 0; t < j; ++t) dd -= 2.0 * vw[t] * vw[nb + t];
+      rowbuf[n] = dd;
+    }
+    if (!grid_barrier(bar, gridDim.x, gen)) return;
   }
 }
 
@@ -575,16 +755,76 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   FTT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   FTT_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // four vectors of n values in shared memory when they fit, three (row and reflector shared) otherwise
-  const bool shared_rk = 4 * sizeof(double) * (size_t)n + 4096 > (size_t)smem_max;
-  const size_t smem = (shared_rk ? 3 : 4) * sizeof(double) * (size_t)n;
-  if (!coop || smem + 4096 > (size_t)smem_max) return false;
+  if (!coop) return false;
   const int64_t nn = (int64_t)n * n;
-  DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s), p((size_t)2 * kMaxSeg * n, s);
+  DBuf<double> A(nn, s), d(n, s), e(n, s), tau(n, s);
   FTT_CUDA(cudaMemcpyAsync(A.get(), G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  // 1. tridiagonalisation
+  constexpr int NW = TridiagWarps<double>::value;
+  // 1a. panels of kPanel columns (blocked), while the matrix after a panel keeps at least
+  //     kPanelTail rows; the symmetric rank-2 kPanel update of each panel on the GEMMs
+  int64_t kb = 0;
+  if (n >= kPanel + kPanelTail) {
+    const size_t smem_p = sizeof(double) * ((size_t)n + 4 * kPanel + 32 * NW);
+    if (smem_p + 4096 > (size_t)smem_max) return false;
+    FTT_CUDA(cudaFuncSetAttribute(tridiag_panel_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max - 4096));
+    int per = 0;
+    FTT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tridiag_panel_kernel<NW>, 32 * NW, smem_p));
+    const int grid = std::min(2, per) * sms;
+    if (grid < 1) return false;
+    const int64_t ps = n + 2 * kPanel;
+    DBuf<double> X(3 * kPanel * (int64_t)n, s), part(kMaxSeg * ps, s), rowbuf(n + 1, s), bpart(grid, s);
+    DBuf<unsigned> bar(4, s);
+    barrier_init_kernel<<<1, 1, 0, s>>>(bar.get(), barrier_spins());
+    FTT_LAUNCH();
+    unsigned gen0 = 0;
+    int nbp = kPanel;
+    int64_t n64 = n;
+    double *Ap = A.get(), *dp = d.get(), *ep = e.get(), *tp = tau.get(), *Xp = X.get(), *pp = part.get(),
+           *rp = rowbuf.get(), *bp = bpart.get();
+    unsigned* brp = bar.get();
+    for (; n - kb - kPanel >= kPanelTail; kb += kPanel) {
+      int64_t k0 = kb;
+      void* args[] = {(void*)&Ap, (void*)&n64, (void*)&k0, (void*)&nbp, (void*)&dp, (void*)&ep, (void*)&tp,
+                      (void*)&Xp, (void*)&pp, (void*)&rp, (void*)&bp, (void*)&brp, (void*)&gen0};
+      double work = 0.0;   // A0 v: 2 m^2; V^T v, W^T v, w and the next row: 12 j m
+      for (int j = 0; j < kPanel; ++j) {
+        const double m = (double)(n - kb - j - 1);
+        work += 2.0 * m * m + 12.0 * j * m;
+      }
+      KClock clk;
+      kclock_begin(clk, KC_TRIDIAG, s);
+      const cudaError_t err = cudaLaunchCooperativeKernel((void*)tridiag_panel_kernel<NW>, dim3(grid),
+                                                          dim3(32 * NW), args, smem_p, s);
+      if (err != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      FTT_LAUNCH();
+      kclock_end(clk, work, s);
+      gen0 += 2 * kPanel;
+      const int64_t k1 = kb + kPanel, M = n - k1;
+      // A0[k1:, k1:] -= [V W] [W V]^T  (rows k1 .. of the panel's vectors)
+      gemm_f64(M, M, 2 * kPanel, -1.0, Xp + k1, 1, n, Xp + kPanel * n64 + k1, n, 1, 1.0, Ap + k1 * n64 + k1, n, 1,
+               s, true);
+    }
+    unsigned hb[4];
+    FTT_CUDA(cudaMemcpyAsync(hb, bar.get(), sizeof(hb), cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    if (hb[2] != 0) {   // a grid barrier gave up: fail with an explicit bound, else the next route
+      note_wait_timeout();
+      if (max_spin() > 0) fail(FASTTT_ETIMEOUT, "a grid barrier of the tridiagonalisation exceeded max_spin polls");
+      return false;
+    }
+  }
+  // 1b. the remaining columns kb .. n-3 unblocked: four vectors of n - kb values in shared
+  //     memory when they fit, three (row and reflector shared) otherwise
   {
-    constexpr int NW = TridiagWarps<double>::value;
+    const size_t cap = (size_t)(n - kb);
+    const bool shared_rk = 4 * sizeof(double) * cap + 4096 > (size_t)smem_max;
+    const size_t smem = (shared_rk ? 3 : 4) * sizeof(double) * cap;
+    if (smem + 4096 > (size_t)smem_max) return false;
+    DBuf<double> p((size_t)2 * kMaxSeg * n, s);
     void* fn = shared_rk ? (void*)tridiag_kernel<double, NW, true> : (void*)tridiag_kernel<double, NW, false>;
     // the route's whole budget (not this call's need), so that concurrent callers never lower it
     FTT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max - 4096));
@@ -595,10 +835,10 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
     DBuf<unsigned> bar(4, s);
     barrier_init_kernel<<<1, 1, 0, s>>>(bar.get(), barrier_spins());
     FTT_LAUNCH();
-    int64_t n64 = n;
+    int64_t n64 = n, k0 = kb;
     double *Ap = A.get(), *dp = d.get(), *ep = e.get(), *tp = tau.get(), *pp = p.get();
     unsigned* bp = bar.get();
-    void* args[] = {(void*)&Ap, (void*)&n64, (void*)&dp, (void*)&ep, (void*)&tp, (void*)&pp, (void*)&bp};
+    void* args[] = {(void*)&Ap, (void*)&n64, (void*)&k0, (void*)&dp, (void*)&ep, (void*)&tp, (void*)&pp, (void*)&bp};
     KClock clk;
     kclock_begin(clk, KC_TRIDIAG, s);
     const cudaError_t err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(32 * NW), args, smem, s);
@@ -607,11 +847,12 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
       return false;
     }
     FTT_LAUNCH();
-    kclock_end(clk, 2.0 * (double)n * (double)n * (double)n, s);   // symv 2m^2 + rank-2 4m^2 per column
+    const double mt = (double)(n - kb);
+    kclock_end(clk, 2.0 * mt * mt * mt, s);   // symv 2m^2 + rank-2 4m^2 per column
     unsigned hb[4];
     FTT_CUDA(cudaMemcpyAsync(hb, bar.get(), sizeof(hb), cudaMemcpyDeviceToHost, s));
     FTT_CUDA(cudaStreamSynchronize(s));
-    if (hb[2] != 0) {   // a grid barrier gave up: fail with an explicit bound, else the next route
+    if (hb[2] != 0) {
       note_wait_timeout();
       if (max_spin() > 0) fail(FASTTT_ETIMEOUT, "a grid barrier of the tridiagonalisation exceeded max_spin polls");
       return false;
@@ -685,7 +926,8 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
       FTT_LAUNCH();
       const double rF = sqrt(frob2(R.get(), kk, s));
       if (!(rF < 0.5)) break;
-      if (rF <= 16.0 * (double)n * 0x1p-53) { ok = true; break; }
+      // 4 n u: the eigenvectors' orthogonality bound is 8 n u, and the back-transformation adds to it
+      if (rF <= 4.0 * (double)n * 0x1p-53) { ok = true; break; }
       FTT_CUDA(cudaMemcpyAsync(Z0.get(), Z.get(), sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
       gemm_f64(n, kv, kv, 0.5, Z0.get(), kv, 1, R.get(), kv, 1, 1.0, Z.get(), kv, 1, s);   // Z += Z R / 2
       ok = (it == 3);
@@ -752,7 +994,8 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
     int64_t n64 = n;
     float *Ap = A.get(), *dp = d.get(), *ep = e.get(), *tp = tau.get(), *pp = p.get();
     unsigned* bp = bar.get();
-    void* args[] = {(void*)&Ap, (void*)&n64, (void*)&dp, (void*)&ep, (void*)&tp, (void*)&pp, (void*)&bp};
+    int64_t k0 = 0;
+    void* args[] = {(void*)&Ap, (void*)&n64, (void*)&k0, (void*)&dp, (void*)&ep, (void*)&tp, (void*)&pp, (void*)&bp};
     KClock clk;
     kclock_begin(clk, KC_TRIDIAG32, s);
     const cudaError_t err =

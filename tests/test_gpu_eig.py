@@ -75,9 +75,12 @@ def test_library_eigensolver(F, kind, n):
     _check(F, _matrix(kind, n, seed=31 + n), "auto")
 
 
+@pytest.mark.parametrize("n", [700, 1500])
 @pytest.mark.parametrize("kind", ["separated", "graded", "sparse_gram"])
-def test_tridiagonal_route_takes_well_separated_spectra(F, kind):
-    _check(F, _matrix(kind, 700, seed=41), "tridiagonal")
+def test_tridiagonal_route_takes_well_separated_spectra(F, kind, n):
+    """n = 700: two blocked panels of 64 columns (panel updates on the DFMA GEMM), the
+    rest unblocked; n = 1500: fifteen panels, updates on the tensor-core slice GEMM."""
+    _check(F, _matrix(kind, n, seed=41), "tridiagonal")
 
 
 @pytest.mark.parametrize("kind", ["clusters", "rank_deficient"])
