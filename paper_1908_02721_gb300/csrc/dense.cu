@@ -1224,12 +1224,12 @@ struct EigStart {
 bool gram_eig(const double* G, int n, double* V, std::vector<double>& h, int64_t max_sweeps, cudaStream_t s,
               bool mixed, EigStart& st0, int64_t& sweeps,
               const std::function<bool(const std::vector<double>&)>& start_ok = nullptr,
-              const std::function<int64_t(const std::vector<double>&)>& topk = nullptr) {
+              const std::function<int64_t(const std::vector<double>&)>& topk = nullptr, int64_t kmax = 0) {
   sweeps = 0;
   const int64_t nn = (int64_t)n * n;
   // few eigenvectors wanted (a rank cap): the FP64 tridiagonal route computes only those
   if (!mixed && topk) {
-    if (sym_eig_tridiag(G, n, V, h, s, false, topk)) {
+    if (sym_eig_tridiag(G, n, V, h, s, false, topk, kmax)) {
       note_eig(true);
       return true;
     }
@@ -1497,7 +1497,7 @@ void sym_eig_iterative(const double* G, int n, double* V, std::vector<double>& l
 
 void svd_from_gram(const double* Gram, int64_t M, int64_t N,
                    const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
-                   SvdOut& out, cudaStream_t s, bool mixed, int64_t kcap) {
+                   SvdOut& out, cudaStream_t s, bool mixed, int64_t kcap, bool partial) {
   if (M > INT32_MAX / 2) fail(FASTTT_ERANK, "SVD too large");
   const int n = (int)M;
   const int nsv = (int)std::min<int64_t>(n, N);
@@ -1541,8 +1541,10 @@ void svd_from_gram(const double* Gram, int64_t M, int64_t N,
   }
   if (!done) {
     int64_t sw = 0;
+    // the rank rule keeps at most kcap: the kcap + 16 largest eigenvalues decide it
     gram_eig(Gram, n, V.get(), h, max_sweeps, s, false, st0, sw, nullptr,
-             capped ? std::function<int64_t(const std::vector<double>&)>(topk) : nullptr);
+             capped ? std::function<int64_t(const std::vector<double>&)>(topk) : nullptr,
+             (capped && partial) ? std::min<int64_t>(n, kcap + 16) : 0);
     out.sweeps = sw;
     sigma_from_lambda(h, out.sigma_all, perm);
     out.sigma_all.resize(nsv);

@@ -105,9 +105,13 @@ void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<in
 // when the route does not apply or its vectors could not be made orthonormal.
 // need (optional): called with the eigenvalues (ascending) before any eigenvector is
 // formed, returns how many of the largest are wanted; only their vectors are computed
-// (the other rows of V are zero).
+// (the other rows of V are zero).  kmax > 0 (with need): need asks for kmax or fewer
+// when the kmax largest eigenvalues are exact, so only those are computed; the others
+// are all set to their mean (the trace of T less the computed ones, capped at the
+// smallest computed one), which keeps every sum of the smallest eigenvalues from the
+// n - kmax smallest up exact.  If need asks for more, the rest are computed.
 bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed,
-                     const std::function<int64_t(const std::vector<double>&)>& need = nullptr);
+                     const std::function<int64_t(const std::vector<double>&)>& need = nullptr, int64_t kmax = 0);
 
 // The FP32 start of the fast eigensolver (tridiag.cu): G scaled by a power of
 // two and rounded to FP32, FP32 Householder tridiagonalisation, bisection and
@@ -135,10 +139,12 @@ void sym_eig_iterative(const double* G, int n, double* V, std::vector<double>& l
 // eigenvalues are zero), r = choose_rank of those.
 // Fills out.r, out.sigma_all, out.sigma and out.U (M x r); out.Vt stays empty.
 // kcap > 0: no rank above kcap will be kept (a rank cap); when it is at most a quarter of
-// M, the FP64 tridiagonal route with only the kept eigenvectors goes first.
+// M, the FP64 tridiagonal route with only the kept eigenvectors goes first, and with
+// partial = true it computes only the kcap + 16 largest eigenvalues (out.sigma_all then
+// holds the mean of the others in their place: exact tail sums, not the values).
 void svd_from_gram(const double* Gram, int64_t M, int64_t N,
                    const std::function<int64_t(const std::vector<double>&)>& choose_rank, int64_t max_sweeps,
-                   SvdOut& out, cudaStream_t s, bool mixed = false, int64_t kcap = 0);
+                   SvdOut& out, cudaStream_t s, bool mixed = false, int64_t kcap = 0, bool partial = false);
 
 // ---------------------------------------------------------------- chol.cu
 

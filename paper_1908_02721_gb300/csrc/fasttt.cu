@@ -602,7 +602,7 @@ void run(int d, const int64_t* dims, int64_t nnz, const int32_t* d_idx, const vo
         {
           DBuf<double> Gram((size_t)M * M, s);
           sb.gram(Gram.get(), s);
-          svd_from_gram(Gram.get(), M, N, choose, max_sweeps, sv, s, mixed, o.max_rank);
+          svd_from_gram(Gram.get(), M, N, choose, max_sweeps, sv, s, mixed, o.max_rank, !o.keep_intermediates);
         }
         sb.project(sv.U.get(), sv.r, W, s);   // W_k = U^T Z = Sigma V^T
         ++st.sparse_bonds;

@@ -411,15 +411,15 @@ __global__ void bisect_kernel(const T* d, const T* e2, int64_t n, T gl, T gu, T 
 // points splitting [lo, hi] into G + 1 equal parts; the Sturm counts (warp ballot)
 // select the part that holds the j-th smallest eigenvalue.  Same result as
 // bisection (down to abstol or adjacent floating-point values) in
-// log_{G+1} instead of log_2 steps.
+// log_{G+1} instead of log_2 steps.  Eigenvalues j0 .. j1-1 of T (order n).
 template <typename T, int G>
 __global__ void __launch_bounds__(256) multisect_kernel(const T* d, const T* e2, int64_t n, T gl, T gu, T pivmin,
-                                                        T abstol, T* lam) {
+                                                        T abstol, T* lam, int64_t j0, int64_t j1) {
   const int lane = threadIdx.x & 31, grp = lane / G, sub = lane % G;
   const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t j = warp_id * (32 / G) + grp;
+  const int64_t j = j0 + warp_id * (32 / G) + grp;   // eigenvalues j0 .. j1-1 of the n
   T lo = gl, hi = gu;
-  bool done = (j >= n);
+  bool done = (j >= j1);
   for (int it = 0; it < 64; ++it) {
     if (!done) {
       const T mid = T(0.5) * (lo + hi);
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) multisect_kernel(const T* d, const T* e2,
       else { lo = nlo; hi = nhi; }
     }
   }
-  if (j < n && sub == 0) lam[j] = T(0.5) * (lo + hi);
+  if (j < j1 && sub == 0) lam[j] = T(0.5) * (lo + hi);
 }
 
 __device__ __forceinline__ double start_component(int64_t i, int64_t j) {
@@ -748,7 +748,7 @@ __global__ void identity64_kernel(double* V, int64_t n) {
 }  // namespace
 
 bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam_out, cudaStream_t s, bool mixed,
-                     const std::function<int64_t(const std::vector<double>&)>& need) {
+                     const std::function<int64_t(const std::vector<double>&)>& need, int64_t kmax) {
   if (n < 3) return false;
   int dev = 0, coop = 0, sms = 0, smem_max = 0;
   FTT_CUDA(cudaGetDevice(&dev));
@@ -883,19 +883,45 @@ bool sym_eig_tridiag(const double* G, int n, double* V, std::vector<double>& lam
   KClock clk2;
   kclock_begin(clk2, KC_TDEIG, s);
   const double abstol = 2.0 * 0x1p-53 * std::max(tnorm, 1e-300);   // the accuracy T carries from step 1
-  multisect_kernel<double, 8><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(d.get(), e2.get(), n, gl, gu, pivmin, abstol,
-                                                                        lam.get());
-  FTT_LAUNCH();
+  // all eigenvalues, or (kmax) the kmax largest: indices j0 .. n-1 of the ascending order
+  const bool partial = need && kmax > 0 && kmax + 8 < n;
+  int64_t j0 = partial ? n - kmax : 0;
+  auto multisect = [&](int64_t a, int64_t b) {   // eigenvalues a .. b-1
+    if (b <= a) return;
+    multisect_kernel<double, 8><<<(unsigned)ceil_div(b - a, 32), 256, 0, s>>>(d.get(), e2.get(), n, gl, gu, pivmin,
+                                                                            abstol, lam.get(), a, b);
+    FTT_LAUNCH();
+  };
+  multisect(j0, n);
   std::vector<double> hl(n);
-  FTT_CUDA(cudaMemcpyAsync(hl.data(), lam.get(), sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  FTT_CUDA(cudaMemcpyAsync(hl.data() + j0, lam.get() + j0, sizeof(double) * (n - j0), cudaMemcpyDeviceToHost, s));
   FTT_CUDA(cudaStreamSynchronize(s));
+  if (j0 > 0) {   // the j0 smallest: their mean from the trace (sum of G's diagonal)
+    std::vector<double> gd(n);
+    FTT_CUDA(cudaMemcpy2DAsync(gd.data(), sizeof(double), G, sizeof(double) * ((size_t)n + 1), sizeof(double), n,
+                               cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    double trace = 0.0, top = 0.0;
+    for (int i = 0; i < n; ++i) trace += gd[i];
+    for (int64_t j = j0; j < n; ++j) top += hl[j];
+    const double mean = std::min((trace - top) / (double)j0, hl[j0]);
+    for (int64_t j = 0; j < j0; ++j) hl[j] = mean;
+  }
   // eigenvectors wanted: the kv largest (all unless the caller needs fewer)
-  const int64_t kv = need ? std::max<int64_t>(1, std::min<int64_t>(n, need(hl))) : n;
+  int64_t kv = need ? std::max<int64_t>(1, std::min<int64_t>(n, need(hl))) : n;
+  if (kv > n - j0) {   // more than were computed: the rest, and the decision again
+    multisect(0, j0);
+    FTT_CUDA(cudaMemcpyAsync(hl.data(), lam.get(), sizeof(double) * j0, cudaMemcpyDeviceToHost, s));
+    FTT_CUDA(cudaStreamSynchronize(s));
+    j0 = 0;
+    kv = std::max<int64_t>(1, std::min<int64_t>(n, need(hl)));
+  }
   const int64_t v0 = n - kv;   // eigenvalues ascending: vectors v0 .. n-1
-  // shifts for inverse iteration: eigenvalues closer than sep are moved apart
+  // shifts for inverse iteration: eigenvalues closer than sep are moved apart (only the
+  // computed ones: the mean that stands in for the others is no shift)
   const double sep = 16.0 * 0x1p-53 * tnorm;
   std::vector<double> hs(hl);
-  for (int i = 1; i < n; ++i)
+  for (int64_t i = std::max<int64_t>(1, j0 + 1); i < n; ++i)
     if (hs[i] - hs[i - 1] < sep) hs[i] = hs[i - 1] + sep;
   FTT_CUDA(cudaMemcpyAsync(shift.get(), hs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
   // 3. eigenvectors of T (Z: n x kv, column c = vector v0 + c), in batches bounding the scratch
@@ -1042,7 +1068,8 @@ bool sym_eig_start_f32(const double* G, int n, double* V, std::vector<double>& l
   kclock_begin(clk2, KC_TDEIG, s);
   const float pivmin = (float)(0x1p-126 * std::max(1.0, emax2));
   multisect_kernel<float, 32><<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(d.get(), e2.get(), n, (float)gl, (float)gu,
-                                                                        pivmin, (float)(2.0 * u32 * tnorm), lam.get());
+                                                                        pivmin, (float)(2.0 * u32 * tnorm), lam.get(), (int64_t)0,
+                                                                        (int64_t)n);
   FTT_LAUNCH();
   std::vector<float> hl(n);
   FTT_CUDA(cudaMemcpyAsync(hl.data(), lam.get(), sizeof(float) * n, cudaMemcpyDeviceToHost, s));

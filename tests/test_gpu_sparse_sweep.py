@@ -107,3 +107,23 @@ def test_sparse_sweep_mode_is_validated(F):
     w = _cases()[0]
     with pytest.raises(F.FastTTError):
         F.fasttt_decompose(w.idx, w.vals, w.dims, 0.1, sparse_sweep="blocks")
+
+
+@pytest.mark.parametrize("case", [1, 3])
+def test_rank_cap_partial_spectrum_matches_oracle(F, case):
+    """A rank cap of 4 on block-sparse bonds whose Grams have order 120 (case 1) or 36
+    (case 3), intermediates not kept: the FP64 tridiagonal route computes only the 20
+    largest eigenvalues (the others stand in as their mean, from the trace) and the
+    vectors kept.  Ranks, the TT and err2 (a tail
+    sum, exact through the trace up to the Gram's rounding) match the oracle."""
+    w = _cases()[case]
+    for p in range(1, w.d - 1):
+        tt = F.fasttt_decompose(w.idx, w.vals, w.dims, 1e-3, p=p, max_rank=4, sparse_sweep="sparse")
+        res = O.fasttt(w.idx, w.vals, w.dims, 1e-3, p=p, max_rank=4)
+        st = tt.stats
+        assert st["sparse_bonds"] == max(0, w.d - 1 - p)
+        assert tt.ranks == res.ranks
+        nA = math.sqrt(res.norm2)
+        assert D.tt_diff_norm(_cores(tt), res.cores) <= TOL * nA
+        assert abs(st["err2"] - res.err2) <= 1e-9 * max(res.err2, 1e-30) + 1e-13 * res.norm2
+        tt.free()
