@@ -12,9 +12,10 @@
 // factorisation and the triangular solves are recursive (halving to 64 x 64
 // leaves): the off-diagonal work is GEMMs (FP64-level slice GEMMs, or FP32-level
 // ones in mixed precision for the Gram and the solve updates), the leaves run in
-// one block's shared memory in FP64.  The triangular solve is a substitution
-// (never an explicit inverse), so the residual Z - R^T Q stays at the rounding
-// level of the products whatever R's condition number.
+// one block's shared memory in FP64 (64 x 64 Cholesky leaves, 32 x 32 solve
+// leaves).  The triangular solve is a substitution (never an explicit inverse), so
+// the residual Z - R^T Q stays at the rounding level of the products whatever R's
+// condition number.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +30,9 @@ namespace fasttt {
 
 namespace {
 
-constexpr int kLeaf = 64;
+constexpr int kLeaf = 64;        // Cholesky leaves
+constexpr int kSolveLeaf = 32;   // triangular-solve leaves: a leaf's FP64 work per column is
+                                 // kSolveLeaf^2 / 2 on one warp, the rest goes to GEMMs
 constexpr int kMaxDevices = 64;
 
 #define CHOL_GRID_STRIDE(i, n)                                                     \
@@ -74,16 +77,16 @@ __global__ void chol_leaf_kernel(double* H, int64_t ld, int nb, double tiny, int
 
 // Forward substitution R^T X = B for the nb x nb upper R at R (leading dimension
 // ldr), B (nb rows x ncols, row stride ldb, unit column stride) overwritten by X.
-// One thread per column of B; the block's NB x 128 tile of B is staged in shared
+// One thread per column of B; the block's NB x TC tile of B is staged in shared
 // memory with all its loads in flight at once, so the substitution chain reads
-// shared memory only, and the solution is kept in registers.
+// shared memory only; the solution overwrites the tile row by row.
 constexpr int kTrsmCols = 128;
-template <int NB>
-__global__ void __launch_bounds__(kTrsmCols) trsm_leaf_kernel(const double* R, int64_t ldr, int nb, double* B,
-                                                              int64_t ldb, int64_t ncols) {
+template <int NB, int TC>
+__global__ void __launch_bounds__(TC) trsm_leaf_kernel(const double* R, int64_t ldr, int nb, double* B,
+                                                       int64_t ldb, int64_t ncols) {
   extern __shared__ double tsm[];
   double(*L)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(tsm);            // L = R^T, identity-padded
-  double(*T)[kTrsmCols + 1] = reinterpret_cast<double(*)[kTrsmCols + 1]>(tsm + NB * (NB + 1));
+  double(*T)[TC + 1] = reinterpret_cast<double(*)[TC + 1]>(tsm + NB * (NB + 1));
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int j = e / NB, i = e % NB;   // consecutive threads read along row j of R
     double v;
@@ -91,30 +94,33 @@ __global__ void __launch_bounds__(kTrsmCols) trsm_leaf_kernel(const double* R, i
     else v = (i == j) ? 1.0 : 0.0;
     L[i][j] = v;
   }
-  const int64_t c0 = (int64_t)blockIdx.x * kTrsmCols;
+  __shared__ double rd[NB];   // reciprocal pivots: one division per row for the whole block
+  const int64_t c0 = (int64_t)blockIdx.x * TC;
   const int64_t c = c0 + threadIdx.x;
   for (int i = 0; i < nb; ++i) T[i][threadIdx.x] = (c < ncols) ? B[(int64_t)i * ldb + c] : 0.0;
   __syncthreads();
+  for (int i = threadIdx.x; i < NB; i += blockDim.x) rd[i] = 1.0 / L[i][i];
+  __syncthreads();
   if (c >= ncols) return;
-  double x[NB];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
+  // row i of the solution overwrites row i of the tile; the loop over i stays rolled (a
+  // fully unrolled 64-step solve is thousands of instructions that every thread runs
+  // once, and fetching them, not the arithmetic, then sets the pace)
+#pragma unroll 1
+  for (int i = 0; i < nb; ++i) {
     // four interleaved partial sums keep the dependent chain a quarter as long
-    double a0 = (i < nb) ? T[i][threadIdx.x] : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-#pragma unroll
-    for (int j = 0; j + 3 < i; j += 4) {
-      a0 -= L[i][j] * x[j];
-      a1 -= L[i][j + 1] * x[j + 1];
-      a2 -= L[i][j + 2] * x[j + 2];
-      a3 -= L[i][j + 3] * x[j + 3];
+    double a0 = T[i][threadIdx.x], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = 0;
+#pragma unroll 2
+    for (; j + 3 < i; j += 4) {
+      a0 -= L[i][j] * T[j][threadIdx.x];
+      a1 -= L[i][j + 1] * T[j + 1][threadIdx.x];
+      a2 -= L[i][j + 2] * T[j + 2][threadIdx.x];
+      a3 -= L[i][j + 3] * T[j + 3][threadIdx.x];
     }
-#pragma unroll
-    for (int j = i & ~3; j < i; ++j) a0 -= L[i][j] * x[j];
-    x[i] = ((a0 + a1) + (a2 + a3)) / L[i][i];
+    for (; j < i; ++j) a0 -= L[i][j] * T[j][threadIdx.x];
+    T[i][threadIdx.x] = ((a0 + a1) + (a2 + a3)) * rd[i];
   }
-#pragma unroll
-  for (int i = 0; i < NB; ++i)
-    if (i < nb) B[(int64_t)i * ldb + c] = x[i];
+  for (int i = 0; i < nb; ++i) B[(int64_t)i * ldb + c] = T[i][threadIdx.x];
 }
 
 // max_i H[i][i] (all >= 0 for a Gram; NaN orders above +inf as bits), as bits
@@ -244,29 +250,38 @@ void cols_times_probes(const double* A, int64_t rows, int64_t cols, int64_t lda,
 
 // ---------------------------------------------------------------- recursive Cholesky / solve
 
-int64_t split_point(int64_t n) { return std::max<int64_t>(kLeaf, (n / 2 / kLeaf) * kLeaf); }
+int64_t split_point(int64_t n, int64_t leaf = kLeaf) { return std::max<int64_t>(leaf, (n / 2 / leaf) * leaf); }
+
+template <int TC>
+void leaf_launch(const double* R, int64_t ldr, int64_t n, double* B, int64_t ldb, int64_t ncols, cudaStream_t s) {
+  const size_t smem = sizeof(double) * ((size_t)kSolveLeaf * (kSolveLeaf + 1) + (size_t)kSolveLeaf * (TC + 1));
+  // the dynamic shared-memory opt-in, once per device (setting it again is harmless)
+  static std::atomic<bool> attr[kMaxDevices];
+  int dev = 0;
+  FTT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices || !attr[dev].load()) {
+    FTT_CUDA(cudaFuncSetAttribute(trsm_leaf_kernel<kSolveLeaf, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    if (dev >= 0 && dev < kMaxDevices) attr[dev].store(true);
+  }
+  trsm_leaf_kernel<kSolveLeaf, TC><<<(unsigned)ceil_div(ncols, TC), TC, smem, s>>>(R, ldr, (int)n, B, ldb, ncols);
+  FTT_LAUNCH();
+}
 
 // R^T X = B in place: R (n x n upper, leading dimension ldr), B (n rows x ncols,
 // row stride ldb).  The update of the lower half of B is a GEMM (FP32-level when mixed).
 void trsm_rt(const double* R, int64_t ldr, int64_t n, double* B, int64_t ldb, int64_t ncols, bool mixed,
              cudaStream_t s) {
   if (n <= 0 || ncols <= 0) return;
-  if (n <= kLeaf) {
-    const size_t smem = sizeof(double) * ((size_t)kLeaf * (kLeaf + 1) + (size_t)kLeaf * (kTrsmCols + 1));
-    // the dynamic shared-memory opt-in, once per device (setting it again is harmless)
-    static std::atomic<bool> attr[kMaxDevices];
-    int dev = 0;
-    FTT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices || !attr[dev].load()) {
-      FTT_CUDA(cudaFuncSetAttribute(trsm_leaf_kernel<kLeaf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      if (dev >= 0 && dev < kMaxDevices) attr[dev].store(true);
-    }
-    trsm_leaf_kernel<kLeaf><<<(unsigned)ceil_div(ncols, kTrsmCols), kTrsmCols, smem, s>>>(R, ldr, (int)n, B, ldb,
-                                                                                          ncols);
-    FTT_LAUNCH();
+  if (n <= kSolveLeaf) {
+    // 128 columns (one per thread) per block when that still fills the SMs twice over,
+    // else 32: the solve is a chain of kSolveLeaf steps per column, so parallelism is in
+    // the columns
+    if (ncols >= 2 * 152 * kTrsmCols) leaf_launch<kTrsmCols>(R, ldr, n, B, ldb, ncols, s);
+    else leaf_launch<32>(R, ldr, n, B, ldb, ncols, s);
     return;
   }
-  const int64_t h = split_point(n);
+  const int64_t h = split_point(n, kSolveLeaf);
   trsm_rt(R, ldr, h, B, ldb, ncols, mixed, s);
   // B2 -= R12^T X1, R12 = R[0:h, h:n]: (R12^T)(i, k) = R[k * ldr + h + i]
   gemm(mixed, n - h, ncols, h, -1.0, R + h, 1, ldr, B, ldb, 1, 1.0, B + h * ldb, ldb, 1, s);

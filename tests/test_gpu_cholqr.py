@@ -10,7 +10,8 @@ checked against bounds of backward-stable arithmetic at the products' precision:
   R upper triangular with a positive diagonal, and equal to LAPACK's R of Z^T
   (signs fixed) within kappa(Z) * 16 M u (the conditioning of the QR factor).
 u = 2^-53 in FP64, 2^-24 for the FP32-level products of the mixed precision.
-Shapes span one 64 x 64 leaf of the recursion, ragged splits and several levels.
+Shapes span one 64 x 64 Cholesky leaf, ragged splits and several levels, and a solve
+wide enough for 128 columns per block.
 """
 import numpy as np
 import pytest
@@ -48,7 +49,7 @@ def _check(F, Z, kappa, precision):
     assert np.linalg.norm(R - Rref) <= kappa * tol * np.linalg.norm(Rref)
 
 
-@pytest.mark.parametrize("M,N", [(1, 5), (64, 64), (100, 300), (257, 1000), (1030, 2100)])
+@pytest.mark.parametrize("M,N", [(1, 5), (64, 64), (100, 300), (257, 1000), (1030, 2100), (100, 40000)])
 @pytest.mark.parametrize("kappa", [1.0, 1e3, 1e6])
 def test_cholqr2_fp64(F, M, N, kappa):
     _check(F, _matrix(M, N, kappa, M + N), kappa, "fp64")
