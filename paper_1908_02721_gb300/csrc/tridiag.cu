@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NW * 32)
   double* red = vw + 2 * nb;                        // NW x 32 partial sums
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * NW + warp, W = (int64_t)gridDim.x * NW;
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, GT = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ps = n + 2 * (int64_t)nb;
   double* Vx = X;
   double* Wx = X + (int64_t)nb * n;
@@ -391,6 +391,37 @@ __device__ int sturm_count(const T* d, const T* e2, int64_t n, T x, T pivmin) {
   return c;
 }
 
+// The same count without a division per step (FP64 division is a sequence of several
+// instructions on the narrow FP64 pipe): the leading principal minors of T - x I,
+//   p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2},   p_{-1} = 1,   p_{-2} = 0,
+// have the pivots above as ratios, q_i = p_i / p_{i-1}, so a negative pivot is a sign
+// change between consecutive minors (Sturm's theorem in the form of Golub & Van Loan,
+// Sec. 8.4.1).  A minor that is exactly zero stands for a negative pivot of magnitude
+// 2^-600 (the guard above, far below any pivot that T's scale produces), so no minor is
+// ever zero; the pair (p_i, p_{i-1}) is scaled by a power of two (exact) whenever p_i's
+// exponent leaves [-256, 256].  Signs and exponents are read from the bit patterns.
+__device__ int sturm_count_minors(const double* d, const double* e2, int64_t n, double x) {
+  int c = 0;
+  double pm = 1.0;       // p_{i-1}
+  double p = d[0] - x;   // p_0
+  if (p == 0.0) p = -0x1p-600;
+  c += (__double_as_longlong(p) < 0);
+  for (int64_t i = 1; i < n; ++i) {
+    double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
+    if (pn == 0.0) pn = -p * 0x1p-600;
+    c += ((__double_as_longlong(pn) ^ __double_as_longlong(p)) < 0);
+    pm = p;
+    p = pn;
+    const int ex = (int)((__double_as_longlong(p) >> 52) & 0x7FF) - 1023;
+    if (ex > 256 || ex < -256) {
+      const double sc = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex, a normal double
+      p *= sc;
+      pm *= sc;
+    }
+  }
+  return c;
+}
+
 // lam[j] = the j-th smallest eigenvalue (j = 0..n-1) by bisection of [gl, gu]
 // down to abstol or adjacent doubles (at most 128 halvings).
 template <typename T>
@@ -427,7 +458,12 @@ __global__ void __launch_bounds__(256) multisect_kernel(const T* d, const T* e2,
     }
     if (__all_sync(0xffffffffu, done)) break;
     const T x = lo + (hi - lo) * (T)(sub + 1) / (T)(G + 1);
-    const bool above = done ? false : (sturm_count(d, e2, n, x, pivmin) > j);
+    int cnt = 0;
+    if (!done) {
+      if constexpr (sizeof(T) == 8) cnt = sturm_count_minors(d, e2, n, x);
+      else cnt = sturm_count(d, e2, n, x, pivmin);
+    }
+    const bool above = done ? false : (cnt > j);
     const unsigned ball = __ballot_sync(0xffffffffu, above);
     if (!done) {
       const unsigned gm = (G == 32) ? ball : ((ball >> (grp * G)) & ((1u << G) - 1u));
