@@ -524,9 +524,10 @@ __device__ void normalise_col(int64_t n, T* z, int64_t ldz) {
   T mx = 0;
   for (int64_t i = 0; i < n; ++i) mx = fmax(mx, fabs(z[i * ldz]));
   if (!(mx > T(0)) || !isfinite(mx)) mx = T(1);
+  const T rmx = T(1) / mx;   // one division: the scaled sum of squares only guards the range
   T nrm = 0;
   for (int64_t i = 0; i < n; ++i) {
-    const T v = z[i * ldz] / mx;
+    const T v = z[i * ldz] * rmx;
     nrm = fma(v, v, nrm);
   }
   const T inv = T(1) / (mx * sqrt(nrm));
@@ -547,18 +548,22 @@ __global__ void inverse_iteration_kernel(const T* d, const T* e, int64_t n, cons
     if (i + 1 < n) { S(sdu, i) = e[i]; S(sdl, i) = e[i]; }
     S(sdu2, i) = T(0);
   }
+  // one division per step: each pivot's reciprocal (pivots below pert in magnitude moved
+  // out to +-pert) is stored in place of the pivot and gives the multiplier as well
+  auto recip = [&](T piv) { return T(1) / ((fabs(piv) < pert) ? copysign(pert, piv) : piv); };
   for (int64_t i = 0; i + 1 < n; ++i) {
     const T di = S(sdd, i), li = S(sdl, i);
     if (fabs(di) >= fabs(li)) {
-      const T piv = (di == T(0)) ? pert : di;
-      S(sdd, i) = piv;
-      const T f = li / piv;
+      const T rp = recip((di == T(0)) ? pert : di);
+      S(sdd, i) = rp;
+      const T f = li * rp;
       S(sdl, i) = f;
       S(sdd, i + 1) = S(sdd, i + 1) - f * S(sdu, i);
       S(spiv, i) = 0;
     } else {
-      const T f = di / li;
-      S(sdd, i) = li;
+      const T rp = recip(li);
+      const T f = di * rp;
+      S(sdd, i) = rp;
       S(sdl, i) = f;
       const T u = S(sdu, i);
       S(sdu, i) = S(sdd, i + 1);
@@ -570,11 +575,7 @@ __global__ void inverse_iteration_kernel(const T* d, const T* e, int64_t n, cons
       S(spiv, i) = 1;
     }
   }
-  for (int64_t i = 0; i < n; ++i) {
-    T piv = S(sdd, i);
-    if (fabs(piv) < pert) piv = copysign(pert, piv);
-    S(sdd, i) = T(1) / piv;   // the solves multiply by the reciprocal pivots
-  }
+  S(sdd, n - 1) = recip(S(sdd, n - 1));   // the solves multiply by the reciprocal pivots
   T* z = Z + (j - zc0);   // vector j in column j - zc0 of Z
   for (int64_t i = 0; i < n; ++i) z[i * ldz] = (T)start_component(i, j);
   for (int it = 0; it < kInvIters; ++it) {
