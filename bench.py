@@ -47,8 +47,11 @@ ERR_BAR = 1e-6                                      # the metric's relative-erro
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the headline step's
 # kernels, from one ncu capture of the headline decomposition (profiles/ has the summary and
 # the command); a kernel changed since the capture has no entry
+TRIDIAG64 = "tridiag_panel_kernel<8>+tridiag_kernel<double,8>"
 NCU_TRAFFIC = {
-    "tridiag_kernel<double>": {"bytes": 168.55e9, "source": "ncu, 2^12 QTT decomposition, 1 launch per step"},
+    TRIDIAG64: {"bytes": 61.88e9,
+                "source": "ncu, 2^12 QTT decomposition, per step: 55 panel launches (61.79 GB read, 0.10 GB "
+                          "written) + 1 unblocked launch (3 MB)"},
 }
 
 
@@ -318,11 +321,15 @@ def _roofline(st, peaks):
     its peak.  The tcgen05 GEMM computes an FP64 product from 8 exact bf16 slices per
     operand: 36 slice-pair products, so its tensor-pipe work is 36 x 2MNK bf16 flops,
     measured against the bf16 dense peak -- the sustained one, as the slice GEMM's launches
-    are spread over the whole step."""
+    are spread over the whole step.  The FP64 tridiagonalisation's work is what its own
+    kernels do on the FP64 pipe: per column of a blocked panel 2m^2 (the product with the
+    matrix as it was at the panel's start) + 12jm (the panel's sums), per column of the
+    unblocked remainder 6m^2; each panel's rank-128 update of the rest is a slice GEMM and
+    counts in that class."""
     bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1921.5))
     classes = {"gemm_f64_kernel": (st["ms_gemm"], st["flop_gemm"], "alu", FP64_PEAK_TFLOPS),
                "jacobi_sweep_kernel<double>": (st["ms_jacobi"], st["flop_jacobi"], "alu", FP64_PEAK_TFLOPS),
-               "tridiag_kernel<double>": (st["ms_tridiag"], st["flop_tridiag"], "alu", FP64_PEAK_TFLOPS),
+               TRIDIAG64: (st["ms_tridiag"], st["flop_tridiag"], "alu", FP64_PEAK_TFLOPS),
                "ozaki_gemm_kernel<8,7,384,64,2>": (st["ms_gemm_oz"], OZ_PAIRS_FP64 * st["flop_gemm_oz"], "tensor",
                                                    bf16_peak),
                "tridiag_kernel<float>": (st["ms_tridiag32"], st["flop_tridiag32"], "alu", FP32_PEAK_TFLOPS),
