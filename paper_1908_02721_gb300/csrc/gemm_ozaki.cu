@@ -371,6 +371,7 @@ __global__ void oz_rowmax_kernel(const double* __restrict__ X, int64_t rows, int
   if (by_row) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
+#pragma unroll 8
     for (int64_t k = k0; k < k1; ++k)
       m = max(m, (unsigned long long)__double_as_longlong(__ldg(X + i + k * s_col)) & kAbsMask);
     if (m) atomicMax(mx + i, m);
@@ -379,6 +380,7 @@ __global__ void oz_rowmax_kernel(const double* __restrict__ X, int64_t rows, int
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= rows) return;
     const double* row = X + i * s_row;
+#pragma unroll 4
     for (int64_t k = k0 + lane; k < k1; k += 32)
       m = max(m, (unsigned long long)__double_as_longlong(__ldg(row + k * s_col)) & kAbsMask);
 #pragma unroll
@@ -494,7 +496,9 @@ void oz_split(const double* X, int64_t rows, int64_t cols, int64_t s_row, int64_
   DBuf<unsigned long long> mx((size_t)rows, s);
   FTT_CUDA(cudaMemsetAsync(mx.get(), 0, mx.bytes(), s));
   const bool by_row = (s_row == 1 && s_col != 1);
-  int64_t kchunk = by_row ? 256 : 2048;
+  // short chunks: a thread's loads form one dependent max chain, so more blocks with
+  // shorter chains finish sooner (one atomic per row and chunk)
+  int64_t kchunk = by_row ? 64 : 512;
   kchunk = std::max<int64_t>(kchunk, ceil_div(cols, 65535));
   const dim3 g1((unsigned)(by_row ? ceil_div(rows, 256) : ceil_div(rows, 8)), (unsigned)ceil_div(cols, kchunk));
   oz_rowmax_kernel<<<g1, 256, 0, s>>>(X, rows, cols, s_row, s_col, kchunk, by_row, mx.get());
