@@ -39,7 +39,7 @@ void ozaki_take_timeout(cudaStream_t s);
 bool ozaki_clear_timeout(cudaStream_t s);
 
 // Products below this many multiply-adds stay on the DFMA / mma.sync kernels.
-constexpr double kTensorGemmMin = 8388608.0;   // 2^23
+constexpr double kTensorGemmMin = 4194304.0;   // 2^22
 
 // The same product as gemm_f64 on the tensor cores: split-TF32 operands (3
 // products), FP32 accumulation, FP64 in and out.  FP32-level accuracy.
