@@ -1,11 +1,16 @@
 // Symmetric eigendecomposition of the Gram matrices of the TT-rounding SVDs
 // (S7-S10) by the textbook dense route (Golub & Van Loan, Matrix Computations,
 // 4th ed., Sec. 8.3 and 8.4):
-//   1. Householder tridiagonalisation A = Q T Q^T, one cooperative kernel; per
-//      column k every block forms the reflector of A[k, k+1:] (identical
-//      fixed-order sums), the grid computes p = tau A22 v, and after a grid
-//      barrier the rank-2 update A22 -= v w^T + w v^T, w = p - (tau/2)(p.v) v.
-//   2. All eigenvalues of T by bisection on Sturm counts (one thread each).
+//   1. Householder tridiagonalisation A = Q T Q^T.  Per column k every block forms
+//      the reflector of A[k, k+1:] (identical fixed-order sums), the grid computes
+//      p = tau A22 v, and the rank-2 update A22 -= v w^T + w v^T,
+//      w = p - (tau/2)(p.v) v, follows.  In FP64, panels of 64 columns are reduced
+//      against the matrix as it was at the panel's start and the panel's updates
+//      applied afterwards as one symmetric GEMM (tridiag_panel_kernel); the last
+//      columns, and the FP32 start, run one cooperative kernel with the update of
+//      column k-1 fused into the product of column k (tridiag_kernel).
+//   2. The eigenvalues of T (all, or the largest a caller needs) by multisection on
+//      Sturm counts.
 //   3. Eigenvectors of T by inverse iteration (one thread each): T - lambda I
 //      factored once with partial pivoting, three solves from a fixed
 //      pseudo-random start; eigenvalues closer than a few ulps of ||T|| are
