@@ -1,19 +1,23 @@
 // Dense FP64 kernels of the TT-rounding stage: a tiled DFMA GEMM with
-// arbitrary element strides, a transpose, and a truncated SVD built on the
-// one-sided (Hestenes) Jacobi method.
+// arbitrary element strides, a transpose, the one-sided (Hestenes) Jacobi SVD and
+// the truncated SVD built on it and on the Gram eigensolvers.
 //
 // The SVD of a row-major M x N matrix Z takes one of two routes:
 //  * direct: one-sided Jacobi on the columns of the tall orientation of Z
-//    (Z itself if M >= N, else Z^T).  Rotations are applied to Z, so singular
-//    values are accurate to a few units of roundoff times sigma_1 (LAPACK-grade);
-//    used while min(M, N) <= kDirectMax.
-//  * Gram: G = Z^T Z (or Z Z^T) by GEMM, then one-sided Jacobi on the symmetric
-//    positive semi-definite G gives its eigenpairs, sigma = sqrt(lambda), and the
-//    other singular vectors by one GEMM.  Singular values below about
-//    sqrt(2^-52) sigma_1 are not resolved on this route.
+//    (Z itself if M >= N, else Z^T); tall-skinny shapes are first reduced to a
+//    small R by Householder TSQR (tsqr.cu) or CholeskyQR2 (chol.cu) and Jacobi
+//    runs on R.  Rotations are applied to the matrix, so singular values are
+//    accurate to a few units of roundoff times sigma_1 (LAPACK-grade); used while
+//    min(M, N) <= kDirectMax, or where a sweep is cheap.
+//  * Gram: G = Z^T Z (or Z Z^T) by GEMM, its eigenpairs from gram_eig (the FP32
+//    tridiagonal start refined with Ogita-Aishima steps on the slice GEMM, else the
+//    FP64 tridiagonal route of tridiag.cu, else an iterative Jacobi solver),
+//    sigma = sqrt(lambda), and the other singular vectors by one GEMM.  Singular
+//    values below about sqrt(2^-52) sigma_1 are not resolved on this route.
 // Jacobi pairs columns by the round-robin (circle) schedule: n/2 disjoint pairs
-// per round, n-1 rounds per sweep, one thread block per pair; sweeps repeat until
-// a whole sweep rotates no pair, or the sweep bound is hit (ETIMEOUT).
+// per round, n-1 rounds per sweep, one warp (columns up to kWarpPairMax) or one
+// thread block per pair; sweeps repeat until a whole sweep rotates no pair, or
+// the sweep bound is hit (ETIMEOUT).
 #include <cuda_runtime.h>
 
 #include <algorithm>
