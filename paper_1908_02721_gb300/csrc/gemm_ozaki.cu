@@ -20,10 +20,11 @@
 // precision): S = 3 slices of b = 8 bits, windows of 192.
 //
 // Tiles: 128 (M) x 64 (N) per CTA; K in stages of 32 (64-byte bf16 rows) through
-// a two-deep shared-memory ring, the S slices of A and of B of a stage loaded by
-// TMA (SWIZZLE_64B, one box per slice) and consumed by K-major SW64 UMMA
-// descriptors; the copy of stage k+1 is issued as soon as the MMAs of stage k-1
-// have released their buffer.  Every mbarrier wait is bounded; a block that gives
+// a two-deep shared-memory ring.  The splitting kernels write every operand as the
+// shared-memory images of its tiles, already in the 64-byte swizzle, so a stage is
+// S contiguous bulk copies (cp.async.bulk) per operand, consumed by K-major SW64
+// UMMA descriptors; the copy of stage k+1 is issued as soon as the MMAs of stage
+// k-1 have released their buffer.  Every mbarrier wait is bounded; a block that gives
 // up raises a sticky device flag, waits (bounded) for its copies and MMAs in
 // flight, frees its TMEM and returns; the call that launched it then fails with
 // FASTTT_ETIMEOUT when the flag is read (ozaki_take_timeout, once per call).
@@ -153,7 +154,8 @@ __host__ __device__ constexpr long long oz_level_max() {
 }
 
 // C tile (128 x 64) of alpha 2^{e_i + f_j} sum_g 2^{-BITS g} L_g + beta C.  K runs
-// in stages of 32 through a two-deep shared-memory ring (TMA, SWIZZLE_64B); the
+// in stages of 32 through a two-deep shared-memory ring (bulk copies of pre-swizzled
+// tile images); the
 // level sums accumulate in TMEM over windows of KD and are then drained exactly
 // into 64-bit integers (KD times the largest level sum per k stays below 2^24).
 template <int S, int BITS, int KD, int BN, int NST>
