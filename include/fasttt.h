@@ -50,13 +50,17 @@ extern "C" {
 
 /* fasttt_opts.precision */
 #define FASTTT_PREC_FP64 0   /* every floating-point step in IEEE FP64 */
-#define FASTTT_PREC_MIXED 1  /* the large contractions (Gram matrices, projections, merges)
-                              * as split-TF32 tensor-core GEMMs with FP32 accumulation and
-                              * tensor-core re-orthonormalisation of the kept factors; Gram
-                              * eigenvectors by FP32 Jacobi; eigenvalues (Rayleigh quotients),
-                              * rank rule, norms and small (direct-route) SVDs in FP64.
-                              * FP32-level accuracy (~1e-6 relative): rank decisions match
-                              * FP64 where the discarded tail is above that level. */
+#define FASTTT_PREC_MIXED 1  /* chosen per bond of the Gram route: the Gram and the
+                              * projection as FP32-level tensor-core products (3 exact bf16
+                              * slices per operand; split TF32 for small products), the
+                              * Gram's distance from the exact one probed, and the bond kept
+                              * at that level only when every kept sigma^2 clears the error
+                              * floor and the rank decision does not move within it; other
+                              * bonds are redone with FP64-level products.  Factors
+                              * re-orthonormalised by CholeskyQR with an FP64 Cholesky;
+                              * eigenvalues, rank rule, norms and the direct-route SVDs in
+                              * FP64.  FP32-level accuracy (~1e-6 relative) on the bonds kept
+                              * at that level; the statistics count both kinds of bond. */
 
 /* fasttt_opts.rounding */
 #define FASTTT_STATIC 0      /* delta_k of eq. (11), Alg. 6 */
