@@ -89,8 +89,8 @@ typedef struct fasttt_opts {
                          FASTTT_ETIMEOUT; 0 = default (2^24 barrier polls, 2^22 pipeline polls) */
 } fasttt_opts;
 
-/* Engine of the dense FP64 contractions.  TENSOR: products of at least 2^26
- * multiply-adds run on the tcgen05 tensor cores from exact bf16 slices of the
+/* Engine of the dense FP64 contractions.  TENSOR: products of at least 2^22
+ * multiply-adds (inner dimension 64 or more) run on the tcgen05 tensor cores from exact bf16 slices of the
  * FP64 operands (8 slices of 7 bits: every slice product exact, the level sums
  * exact in FP32 over windows of 384 and then in 64-bit integers; FP64-level
  * results, Ozaki-Ogita-Oishi-Rump splitting), smaller ones on FP64 DFMA.  DFMA:

@@ -88,20 +88,22 @@ struct SvdOut {
   DBuf<double> U, sigma, Vt;
   int64_t sweeps = 0;
 };
-// mixed = true: the Gram and the projections run on the tensor cores
-// (gemm_tf32x3, FP32-level accuracy), the n x n eigenproblem of large Grams in
-// FP32 Jacobi with FP64 Rayleigh quotients; the direct route stays FP64.
+// mixed = true: the Gram and the projections are FP32-level tensor-core products
+// (3 exact bf16 slices, or split TF32 for small products), the Gram's eigenpairs
+// from the FP32 start refined with FP32-level products, and the bond is redone with
+// FP64-level products when that level cannot decide its rank; the direct route
+// stays FP64.
 // ortho = 1 (left): U must come out orthonormal; 2 (right): the rows of Vt must.
 // In mixed precision the factor that the tall-side product amplifies by
-// sigma_1 / sigma_r is re-orthonormalised on the tensor cores and its partner
-// recomputed (the re-orthogonalisation that keeps FP32-level products usable).
+// sigma_1 / sigma_r is re-orthonormalised by CholeskyQR (FP64 Cholesky) and its
+// partner recomputed (the re-orthogonalisation that keeps FP32-level products usable).
 void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<int64_t(const std::vector<double>&)>& choose_rank,
                    int64_t max_sweeps, SvdOut& out, cudaStream_t s, bool mixed = false, int ortho = 0);
 
 // Eigendecomposition of the symmetric n x n G (row-major FP64) by Householder
 // tridiagonalisation, bisection and inverse iteration (tridiag.cu).  V (n x n)
 // receives eigenvector j in V[j*n .. j*n + n), lam_out the eigenvalues.  mixed:
-// the back-transformation GEMMs run split-TF32.  Returns false (V undefined)
+// the back-transformation GEMMs run at FP32 level.  Returns false (V undefined)
 // when the route does not apply or its vectors could not be made orthonormal.
 // need (optional): called with the eigenvalues (ascending) before any eigenvector is
 // formed, returns how many of the largest are wanted; only their vectors are computed
