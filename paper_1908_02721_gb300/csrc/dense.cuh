@@ -101,7 +101,7 @@ void svd_truncated(const double* Z, int64_t M, int64_t N, const std::function<in
                    int64_t max_sweeps, SvdOut& out, cudaStream_t s, bool mixed = false, int ortho = 0);
 
 // Eigendecomposition of the symmetric n x n G (row-major FP64) by Householder
-// tridiagonalisation, bisection and inverse iteration (tridiag.cu).  V (n x n)
+// tridiagonalisation, multisection and inverse iteration (tridiag.cu).  V (n x n)
 // receives eigenvector j in V[j*n .. j*n + n), lam_out the eigenvalues.  mixed:
 // the back-transformation GEMMs run at FP32 level.  Returns false (V undefined)
 // when the route does not apply or its vectors could not be made orthonormal.
